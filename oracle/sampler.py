@@ -1,0 +1,238 @@
+"""InfiniteDiffusion sampling (oracle): lazy Alg. 1 and eager Eq. 1, FP64.
+
+Test infrastructure (see the package header).
+
+Indexing.  The paper counts steps down (J_T noise, J_0 result, query J_t from
+J_{t+1}); this module counts up: J_0 = sigma_0 N(seed, level, 0, .) is the
+paper's J_T, step k maps J_k to J_{k+1}, and J_K is the result (paper J_0).
+
+One blended step (Sec. 3.1-3.3).  Each window i of step k applies Phi, one
+sampler step of the window: with x = J_k[R_i],
+    Phi_i = D(x; sigma_k) + sigma_{k+1} N(seed, level, k+1, R_i)   (k+1 < K)
+    Phi_i = D(x; sigma_k)                                          (k+1 = K)
+D the EDM-preconditioned denoiser (oracle.schedule).  The update is Eq. 2:
+J_{k+1}[R] = (sum_{i in kappa(R)} U_i(W (x) Phi_i)) / (sum_{j in kappa(R)} U_j(W))
+restricted to R, division by zero taken as zero (App. B).  Because the noise
+is keyed on absolute coordinates, this equals blending D alone and adding the
+noise once per pixel; the CUDA path uses that fused form.
+
+* ``Level`` is Alg. 1 literally: per step, A and B are kept as per-window
+  contributions (i, W (x) Phi_i) with the processed set P given by the keys
+  present, an LRU per step of bounded capacity, and eviction that removes i
+  from P (Sec. 3.3 "To keep storage bounded ...").  Contributions are summed
+  in the canonical order of kappa (row index i, then column index j).
+* ``eager_level`` is Eq. 1 (bounded MultiDiffusion): every window lying
+  inside a canvas that holds the whole dependency cone, all steps dense.
+* ``World`` chains levels as a DAG (App. C.3): the fine level's conditioning
+  channel is the nearest x scale upsampling of the coarse level's result
+  (Sec. 5.3, decoder conditioning), fetched lazily.
+
+Pins: the two routes agree (Lemma 3); query-order and cache-size
+independence (Thm 1); closed forms with the test denoisers; window counts of
+Lemma 4 / Thm 2 (tests/test_oracle_sampler.py).
+"""
+from __future__ import annotations
+
+from collections import OrderedDict
+
+import numpy as np
+
+from . import kappa as K_
+from . import noise as N_
+from . import schedule as S_
+from . import unet as U_
+
+
+class _LevelCommon:
+    def __init__(self, seed: int, lv: dict, level_index: int, weights=None,
+                 blend_eps: float = 1e-3, parent=None):
+        self.seed = int(seed)
+        self.lv = dict(lv)
+        self.level_index = int(level_index)
+        self.H = int(lv["window"])
+        self.s = int(lv["stride"])
+        self.o = int(lv.get("offset", 0))
+        self.K = int(lv["steps"])
+        self.sig = S_.sigmas(self.K, lv["sigma_max"], lv["sigma_min"], lv["rho"])
+        self.sd = float(lv["sigma_data"])
+        self.W = S_.weight_2d(self.H, blend_eps)
+        self.params = None
+        if int(lv.get("test_denoiser", 0)) == 0:
+            self.params = U_.unpack(lv, weights)
+        self.parent = parent
+        self.scale = int(lv.get("scale_to_parent", 0))
+        self.phi_calls = 0
+
+    def noise(self, step, y0, x0, h, w):
+        return N_.normal_region(self.seed, self.level_index, step, x0, y0, w, h).astype(np.float64)
+
+    def cond(self, y0, x0, h, w):
+        """Nearest-neighbour upsampled parent result over the fine rect."""
+        f = self.scale
+        cy0, cx0 = y0 // f, x0 // f
+        cy1, cx1 = (y0 + h - 1) // f, (x0 + w - 1) // f
+        P = self.parent.final(cy0, cx0, cy1 - cy0 + 1, cx1 - cx0 + 1)
+        ys = (np.arange(y0, y0 + h) // f) - cy0
+        xs = (np.arange(x0, x0 + w) // f) - cx0
+        return P[np.ix_(ys, xs)]
+
+    def phi(self, k: int, xs: list, rects: list) -> list:
+        """Phi for the windows of step k: inputs xs (H x H each) at rects."""
+        c_skip, c_out, c_in = S_.edm_coeffs(self.sig[k], self.sd)
+        chans = [np.stack(xs)[:, None] * c_in]
+        if int(self.lv["in_ch"]) == 2:
+            chans.append(np.stack([self.cond(*r) for r in rects])[:, None])
+        xin = np.concatenate(chans, axis=1)
+        F = np.empty((len(xs), self.H, self.H))
+        bs = 64 if self.H <= 32 else 1
+        for b0 in range(0, len(xs), bs):
+            F[b0:b0 + bs] = U_.forward(self.lv, self.params, xin[b0:b0 + bs])[:, 0]
+        self.phi_calls += len(xs)
+        out = []
+        for x, r, f in zip(xs, rects, F):
+            d = c_skip * x + c_out * f
+            if k + 1 < self.K:
+                d = d + self.sig[k + 1] * self.noise(k + 1, *r)
+            out.append(d)
+        return out
+
+
+class Level(_LevelCommon):
+    """Lazy InfiniteDiffusion (Alg. 1) for one level of the stack."""
+
+    def __init__(self, *a, capacity=None, **kw):
+        super().__init__(*a, **kw)
+        self.capacity = capacity          # per-step contribution LRU capacity (None = unbounded)
+        self.contrib = [OrderedDict() for _ in range(self.K + 1)]  # step -> {(i,j): W (x) Phi}
+
+    def clear(self):
+        for c in self.contrib:
+            c.clear()
+
+    def J(self, k: int, y0: int, x0: int, h: int, w: int) -> np.ndarray:
+        if k == 0:
+            return self.sig[0] * self.noise(0, y0, x0, h, w)
+        win = K_.kappa(y0, x0, h, w, self.H, self.s, self.o)
+        store = self.contrib[k]
+        todo = [i for i in win if i not in store]
+        if todo:
+            rects = [K_.window_rect(i, j, self.H, self.s, self.o) for (i, j) in todo]
+            xs = [self.J(k - 1, *r) for r in rects]
+            phis = self.phi(k - 1, xs, rects)
+            for key, p in zip(todo, phis):
+                store[key] = self.W * p
+        A = np.zeros((h, w))
+        B = np.zeros((h, w))
+        for (i, j) in win:
+            store.move_to_end((i, j))
+            wy, wx, _, _ = K_.window_rect(i, j, self.H, self.s, self.o)
+            ya, yb = max(y0, wy), min(y0 + h, wy + self.H)
+            xa, xb = max(x0, wx), min(x0 + w, wx + self.H)
+            A[ya - y0:yb - y0, xa - x0:xb - x0] += store[(i, j)][ya - wy:yb - wy, xa - wx:xb - wx]
+            B[ya - y0:yb - y0, xa - x0:xb - x0] += self.W[ya - wy:yb - wy, xa - wx:xb - wx]
+        if self.capacity is not None:
+            while len(store) > self.capacity:
+                store.popitem(last=False)     # evict (i, x_i): i leaves P_k
+        out = np.zeros((h, w))
+        nz = B != 0
+        out[nz] = A[nz] / B[nz]
+        return out
+
+    def final(self, y0, x0, h, w):
+        return self.J(self.K, y0, x0, h, w)
+
+
+def cone_rects(lvl: _LevelCommon, y0, x0, h, w):
+    """rects[k] = region of J_k a cold query of J_K[R] touches."""
+    rects = [None] * (lvl.K + 1)
+    rects[lvl.K] = (y0, x0, h, w)
+    for k in range(lvl.K, 0, -1):
+        ry0, rx0, rh, rw = rects[k]
+        ri = K_.kappa_1d(ry0, ry0 + rh, lvl.H, lvl.s, lvl.o)
+        rj = K_.kappa_1d(rx0, rx0 + rw, lvl.H, lvl.s, lvl.o)
+        rects[k - 1] = (ri[0] * lvl.s + lvl.o, rj[0] * lvl.s + lvl.o,
+                        (ri[1] - ri[0]) * lvl.s + lvl.H, (rj[1] - rj[0]) * lvl.s + lvl.H)
+    return rects
+
+
+class EagerLevel(_LevelCommon):
+    """Eq. 1 on a bounded canvas holding the cone of one region, all steps dense."""
+
+    def run(self, y0, x0, h, w):
+        rects = cone_rects(self, y0, x0, h, w)
+        cy, cx, ch, cw = rects[0]
+        J = self.sig[0] * self.noise(0, cy, cx, ch, cw)
+        ni = (ch - self.H) // self.s + 1
+        nj = (cw - self.H) // self.s + 1
+        i0 = (cy - self.o) // self.s
+        j0 = (cx - self.o) // self.s
+        wins = [(i0 + a, j0 + b) for a in range(ni) for b in range(nj)]
+        rr = [K_.window_rect(i, j, self.H, self.s, self.o) for (i, j) in wins]
+        for k in range(self.K):
+            xs = [J[r[0] - cy:r[0] - cy + self.H, r[1] - cx:r[1] - cx + self.H] for r in rr]
+            phis = self.phi(k, xs, rr)
+            A = np.zeros((ch, cw))
+            B = np.zeros((ch, cw))
+            for r, p in zip(rr, phis):
+                A[r[0] - cy:r[0] - cy + self.H, r[1] - cx:r[1] - cx + self.H] += self.W * p
+                B[r[0] - cy:r[0] - cy + self.H, r[1] - cx:r[1] - cx + self.H] += self.W
+            J = np.zeros((ch, cw))
+            nz = B != 0
+            J[nz] = A[nz] / B[nz]
+        self._canvas = (cy, cx, J)
+        return J[y0 - cy:y0 - cy + h, x0 - cx:x0 - cx + w]
+
+    def final(self, y0, x0, h, w):
+        cy, cx, J = self._canvas
+        assert y0 >= cy and x0 >= cx and y0 + h <= cy + J.shape[0] and x0 + w <= cx + J.shape[1]
+        return J[y0 - cy:y0 - cy + h, x0 - cx:x0 - cx + w]
+
+
+class World:
+    """A model stack (coarse level first) with lazy levels and the Laplacian decode."""
+
+    def __init__(self, seed: int, stack: dict, weights: list, capacity=None):
+        self.stack = stack
+        self.levels = []
+        parent = None
+        for li, lv in enumerate(stack["level"]):
+            lvl = Level(seed, lv, li, weights=weights[li] if weights else None,
+                        blend_eps=stack.get("blend_eps", 1e-3), parent=parent,
+                        capacity=capacity)
+            self.levels.append(lvl)
+            parent = lvl
+
+    def model(self, y0, x0, h, w):
+        """Result J_K of the last level over the region (model units)."""
+        return self.levels[-1].final(y0, x0, h, w)
+
+    def metres(self, y0, x0, h, w):
+        from . import laplacian as L_
+        st = self.stack
+        coarse, fine = self.levels[0], self.levels[-1]
+        return L_.decode_metres(coarse.final, fine.final, y0, x0, h, w,
+                                factor=st["lap_factor"], blur_sigma=st["lap_blur_sigma"],
+                                radius=st["lap_radius"], low_mu=st["low_mu"],
+                                low_scale=st["low_scale"], res_scale=st["res_scale"])
+
+
+def eager_world_model(seed: int, stack: dict, weights: list, y0, x0, h, w):
+    """Eq. 1 brute force for the last level's result over a region; for a
+    two-level stack the coarse level runs eagerly over the canvas the fine
+    cone's conditioning needs."""
+    lvls = stack["level"]
+    eps = stack.get("blend_eps", 1e-3)
+    if len(lvls) == 1:
+        e = EagerLevel(seed, lvls[0], 0, weights=weights[0] if weights else None, blend_eps=eps)
+        return e.run(y0, x0, h, w)
+    fine_lv = lvls[1]
+    fine = EagerLevel(seed, fine_lv, 1, weights=weights[1] if weights else None, blend_eps=eps)
+    rects = cone_rects(fine, y0, x0, h, w)
+    cy, cx, ch, cw = rects[0]
+    f = int(fine_lv["scale_to_parent"])
+    coarse = EagerLevel(seed, lvls[0], 0, weights=weights[0] if weights else None, blend_eps=eps)
+    qy0, qx0 = cy // f, cx // f
+    qy1, qx1 = (cy + ch - 1) // f, (cx + cw - 1) // f
+    coarse.run(qy0, qx0, qy1 - qy0 + 1, qx1 - qx0 + 1)
+    fine.parent = coarse
+    return fine.run(y0, x0, h, w)

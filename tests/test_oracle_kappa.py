@@ -1,0 +1,55 @@
+"""Pins of kappa (Alg. 3) and of cone window counts (Lemma 4 / Thm 2)."""
+import random
+
+from oracle import kappa as K
+
+
+def brute_kappa(y0, x0, h, w, size, stride, offset, span=60):
+    out = []
+    for i in range(-span, span):
+        for j in range(-span, span):
+            wy, wx = i * stride + offset, j * stride + offset
+            if wy < y0 + h and y0 < wy + size and wx < x0 + w and x0 < wx + size:
+                out.append((i, j))
+    return out
+
+
+def test_kappa_brute_force():
+    rnd = random.Random(0)
+    for _ in range(400):
+        size = rnd.randint(1, 12)
+        stride = rnd.randint(1, 12)
+        offset = rnd.randint(-7, 7)
+        y0, x0 = rnd.randint(-70, 60), rnd.randint(-70, 60)
+        h, w = rnd.randint(1, 20), rnd.randint(1, 20)
+        assert K.kappa(y0, x0, h, w, size, stride, offset) == brute_kappa(y0, x0, h, w, size, stride, offset, 200)
+
+
+def test_kappa_gap_between_windows_is_empty():
+    # stride larger than the window leaves pixels covered by no window
+    assert K.kappa(5, 5, 1, 1, size=4, stride=10) == []
+    assert K.kappa_1d(4, 10, 4, 10) is None
+    assert K.kappa_1d(-3, -1, 4, 10) is None   # pixels -3,-2 lie in the gap [-6, 0)
+
+
+def test_cone_counts_closed_form():
+    # n x n tiles (tile = stride, window = 2 stride) aligned query: the last
+    # step needs (n+1)^2 windows and each earlier step two more per side.
+    for (n, s, K_) in [(4, 16, 4), (3, 8, 5), (1, 64, 20)]:
+        counts = K.cone_window_counts(0, 0, n * s, n * s, 2 * s, s, K_)
+        assert counts == [(n + 2 * k + 1) ** 2 for k in range(K_)]
+    # the 64 x 64 query at the origin, 32/16 windows, 4 steps: 276 windows
+    assert sum(K.cone_window_counts(0, 0, 64, 64, 32, 16, 4)) == 276
+
+
+def test_cone_counts_bounded_independent_of_location():
+    # Thm 2: cost of a window-sized query is bounded by M + M^2 + ... + M^T,
+    # with M = |kappa(R_i)| = 9 for 50% overlap; and it is translation invariant
+    rnd = random.Random(1)
+    ref = None
+    for _ in range(50):
+        i, j = rnd.randint(-10 ** 6, 10 ** 6), rnd.randint(-10 ** 6, 10 ** 6)
+        c = K.cone_window_counts(i * 16, j * 16, 32, 32, 32, 16, 4)
+        ref = ref or c
+        assert c == ref
+        assert sum(c) <= 9 + 9 ** 2 + 9 ** 3 + 9 ** 4

@@ -1,0 +1,161 @@
+"""Pins of the oracle sampler: closed forms, Lemma 3 (lazy == eager),
+Thm 1 (order / cache independence), window accounting (Lemma 4)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import kappa as K
+from oracle import noise as N
+from oracle import sampler as S
+from oracle import schedule as Sc
+from oracle import unet as U
+
+
+def _weights(st, seed=0):
+    return [synth.weights([s for _, s in U.param_shapes(lv)], seed, li) for li, lv in enumerate(st["level"])]
+
+
+# ----------------------------------------------------------- schedule pieces
+
+def test_sigma_schedule():
+    s = Sc.sigmas(4, 80.0, 0.02, 7.0)
+    assert s[0] == pytest.approx(80.0, rel=1e-15) and s[-1] == pytest.approx(0.02, rel=1e-12)
+    assert np.all(np.diff(s) < 0)
+    assert s[1] == pytest.approx(12.67583, rel=1e-5) and s[2] == pytest.approx(1.032751, rel=1e-5)
+    s20 = Sc.sigmas(20, 80.0, 0.02, 7.0)
+    assert s20[1] == pytest.approx(61.650, rel=1e-4) and s20[-2] == pytest.approx(0.04407, rel=1e-3)
+
+
+def test_edm_identity():
+    # c_skip + c_out^2 / sd^2 = 1 and c_in^2 (sigma^2 + sd^2) = 1
+    for sig in [80.0, 1.0, 0.02]:
+        cs, co, ci = Sc.edm_coeffs(sig, 0.5)
+        assert cs + co * co / 0.25 == pytest.approx(1.0, abs=1e-14)
+        assert ci * ci * (sig * sig + 0.25) == pytest.approx(1.0, abs=1e-14)
+
+
+def test_weight_window_and_denominator():
+    for s in (16, 64, 5):
+        H = 2 * s
+        w = Sc.weight_1d(H, 1e-3)
+        assert w[0] == pytest.approx(1e-3) and w[-1] == pytest.approx(1e-3)
+        assert np.all(w <= 1.0) and np.all(w > 0)
+        # per-axis sum of the two windows covering a pixel is constant
+        B1 = w[:s] + w[s:]
+        assert np.allclose(B1, 2.0 - (1.0 - 1e-3) * s / (s - 0.5), rtol=1e-14)
+    assert 2.0 - 0.999 * 16 / 15.5 == pytest.approx(0.9687742, abs=1e-7)
+
+
+# ----------------------------------------------------------- closed forms
+
+def _closed_form_pixelwise(lv, seed, level_index, y0, x0, h, w, F_of_J):
+    """J_{k+1} = c_skip J_k + c_out Fbar_k + sigma_{k+1} N per pixel."""
+    K_ = lv["steps"]
+    sig = Sc.sigmas(K_, lv["sigma_max"], lv["sigma_min"], lv["rho"])
+    J = sig[0] * N.normal_region(seed, level_index, 0, x0, y0, w, h).astype(np.float64)
+    for k in range(K_):
+        cs, co, ci = Sc.edm_coeffs(sig[k], lv["sigma_data"])
+        J = cs * J + co * F_of_J(J, ci, k)
+        if k + 1 < K_:
+            J = J + sig[k + 1] * N.normal_region(seed, level_index, k + 1, x0, y0, w, h)
+    return J
+
+
+@pytest.mark.parametrize("td", [1, 2])
+def test_constant_and_identity_denoisers_closed_form(td):
+    st = synth.config1_stack(test_denoiser=td)
+    lv = st["level"][0]
+    world = S.World(3, st, None)
+    got = world.model(-40, 17, 37, 29)
+    F = (lambda J, ci, k: 0.5) if td == 1 else (lambda J, ci, k: ci * J)
+    ref = _closed_form_pixelwise(lv, 3, 0, -40, 17, 37, 29, F)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_local_coordinate_denoiser_closed_form():
+    # F = c_in J + u/H - 2 v/H: the blend adds sum_i W_i g_i / sum_i W_i with g
+    # the window-local coordinate term, written out here per pixel.
+    st = synth.config1_stack(test_denoiser=3)
+    lv = st["level"][0]
+    H, s = lv["window"], lv["stride"]
+    world = S.World(5, st, None)
+    y0, x0, h, w = -23, 40, 19, 21
+    got = world.model(y0, x0, h, w)
+    w1 = Sc.weight_1d(H, 1e-3)
+    g = np.zeros((h, w))
+    for a in range(h):
+        Y = y0 + a
+        for b in range(w):
+            X = x0 + b
+            num = den = 0.0
+            for i in range(Y // s - 1, Y // s + 1):
+                for j in range(X // s - 1, X // s + 1):
+                    u, v = Y - i * s, X - j * s
+                    ww = w1[u] * w1[v]
+                    num += ww * (u / H - 2.0 * v / H)
+                    den += ww
+            g[a, b] = num / den
+    ref = _closed_form_pixelwise(lv, 5, 0, y0, x0, h, w, lambda J, ci, k: ci * J + g)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+# ----------------------------------------------------------- lazy == eager
+
+def test_lazy_equals_eager_config1_arch():
+    st = synth.with_steps(synth.config1_stack(), 2)
+    wts = _weights(st)
+    lazy = S.World(0, st, wts).model(-5, 9, 20, 23)
+    eager = S.eager_world_model(0, st, wts, -5, 9, 20, 23)
+    assert np.max(np.abs(lazy - eager)) <= 1e-12 * np.max(np.abs(eager))
+
+
+def test_lazy_equals_eager_two_level():
+    st = synth.small_hier_stack(steps=2, window=16, stride=8, coarse_channels=(8, 8),
+                                fine_channels=(8, 8))
+    wts = _weights(st)
+    lazy = S.World(1, st, wts).model(3, -20, 12, 10)
+    eager = S.eager_world_model(1, st, wts, 3, -20, 12, 10)
+    assert np.max(np.abs(lazy - eager)) <= 1e-12 * np.max(np.abs(eager))
+
+
+# ----------------------------------------------------------- Thm 1, Lemma 4
+
+def test_order_and_cache_independence():
+    st = synth.with_steps(synth.config1_stack(), 3)
+    wts = _weights(st)
+    r1, r2 = (0, 0, 40, 40), (20, 24, 40, 30)
+    a = S.World(0, st, wts)
+    a1, a2 = a.model(*r1), a.model(*r2)
+    b = S.World(0, st, wts)
+    b2, b1 = b.model(*r2), b.model(*r1)
+    assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
+    # overlap agreement
+    assert np.array_equal(a1[20:40, 24:40], a2[0:20, 0:16])
+    for cap in (0, 1, 5):
+        c = S.World(0, st, wts, capacity=cap)
+        c.model(*r2)
+        assert np.array_equal(c.model(*r1), a1)
+
+
+def test_phi_call_accounting():
+    st = synth.config1_stack(test_denoiser=1)
+    world = S.World(0, st, None)
+    world.model(0, 0, 64, 64)
+    lvl = world.levels[0]
+    assert lvl.phi_calls == 276
+    # a repeated query is served from the contributions: no new Phi calls
+    world.model(0, 0, 64, 64)
+    assert lvl.phi_calls == 276
+    # a neighbouring 64x64 query reuses overlapping windows
+    world.model(0, 64, 64, 64)
+    assert lvl.phi_calls < 2 * 276
+
+
+def test_division_by_zero_is_zero():
+    # stride > window leaves uncovered pixels: B = 0 there and J is defined as 0
+    lv = synth.level(window=4, stride=6, steps=1, test_denoiser=1)
+    world = S.World(0, synth.stack([lv]), None)
+    out = world.model(0, 0, 1, 12)[0]
+    assert np.all(out[4:6] == 0.0) and np.all(out[0:4] != 0.0)

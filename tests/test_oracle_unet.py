@@ -1,0 +1,91 @@
+"""Pin of the oracle UNet against torch.nn.functional in FP64 (library routines)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as TF
+
+import synth
+from oracle import unet as U
+
+
+def torch_forward(lv, p, x):
+    """The same network written with torch.nn.functional layers (FP64)."""
+    G = lv["gn_groups"]
+    t = {k: torch.from_numpy(v) for k, v in p.items()}
+
+    def gn(h):
+        return TF.group_norm(h, G, eps=1e-5)
+
+    def conv(h, w):
+        return TF.conv2d(h, w, padding=w.shape[-1] // 2)
+
+    def rb(h, name):
+        a = conv(TF.silu(gn(h)), t[name + ".conv1"])
+        a = conv(TF.silu(gn(a)), t[name + ".conv2"])
+        return a + (conv(h, t[name + ".skip"]) if name + ".skip" in t else h)
+
+    h = conv(torch.from_numpy(x), t["in_conv"])
+    skips = []
+    L = lv["levels"]
+    for l in range(L):
+        h = rb(h, f"enc{l}")
+        skips.append(h)
+        if l < L - 1:
+            h = TF.avg_pool2d(h, 2)
+    if lv["attn_at_bottom"]:
+        B, C, Hh, Ww = h.shape
+        heads = lv["attn_heads"]
+        d = C // heads
+        qkv = conv(gn(h), t["attn.qkv"]).reshape(B, 3, heads, d, Hh * Ww)
+        q, k, v = qkv[:, 0].transpose(-1, -2), qkv[:, 1].transpose(-1, -2), qkv[:, 2].transpose(-1, -2)
+        a = torch.softmax(q @ k.transpose(-1, -2) / math.sqrt(d), dim=-1)
+        o = (a @ v).transpose(-1, -2).reshape(B, C, Hh, Ww)
+        h = h + conv(o, t["attn.proj"])
+    h = rb(h, "mid")
+    for l in range(L - 2, -1, -1):
+        h = torch.cat([TF.interpolate(h, scale_factor=2, mode="nearest"), skips[l]], dim=1)
+        h = rb(h, f"dec{l}")
+    return conv(TF.silu(gn(h)), t["out_conv"]).numpy()
+
+
+@pytest.mark.parametrize("lv", [
+    synth.config1_stack()["level"][0],
+    synth.small_hier_stack()["level"][1],
+    synth.level(levels=3, channels=(8, 16, 16), in_ch=2, attn_at_bottom=1, attn_heads=2, window=16),
+])
+def test_unet_matches_torch_functional(lv):
+    shapes = [s for _, s in U.param_shapes(lv)]
+    w = synth.weights(shapes, 0, 0)
+    p = U.unpack(lv, w)
+    x = synth.window_batch(3, lv["in_ch"], lv["window"], seed=1, scale=2.0).astype(np.float64)
+    got = U.forward(lv, p, x)
+    ref = torch_forward(lv, p, x)
+    assert got.shape == (3, lv["out_ch"], lv["window"], lv["window"])
+    assert np.max(np.abs(got - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_param_count_and_flops_config1():
+    lv = synth.config1_stack()["level"][0]
+    names = [n for n, _ in U.param_shapes(lv)]
+    assert names == ["in_conv", "enc0.conv1", "enc0.conv2", "enc1.conv1", "enc1.conv2",
+                     "mid.conv1", "mid.conv2", "dec0.conv1", "dec0.conv2", "dec0.skip", "out_conv"]
+    # 29.95 MFLOP per 32x32 window (convolutions, 2 FLOP per MAC)
+    assert abs(U.flops_per_window(lv) / 1e6 - 29.95) < 0.01
+
+
+def test_flops_config2():
+    st = synth.config2_stack()
+    fine = U.flops_per_window(st["level"][1]) / 1e9
+    coarse = U.flops_per_window(st["level"][0]) / 1e9
+    assert abs(fine - 22.0) < 0.1 and abs(coarse - 14.67) < 0.1
+
+
+def test_conv_is_cross_correlation():
+    # a kernel with a single 1 at the top-left tap shifts the image by (+1, +1)
+    x = np.arange(16, dtype=np.float64).reshape(1, 1, 4, 4)
+    w = np.zeros((1, 1, 3, 3))
+    w[0, 0, 0, 0] = 1.0
+    y = U.conv(x, w)[0, 0]
+    assert y[1, 1] == x[0, 0, 0, 0] and y[0, 0] == 0.0 and y[3, 3] == x[0, 0, 2, 2]
