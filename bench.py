@@ -1,0 +1,435 @@
+"""Benchmark of the InfiniteDiffusion sampling path on GB300.
+
+One step = one cold query of a 4096 x 4096 heightmap in metres through the
+two-level stack (coarse UNet 64/128/128 at 1/8 resolution conditioning a fine
+UNet 64/128/256/256 with bottom attention, 128-pixel windows at stride 64, 20
+blended steps per level, Laplacian decode): noise, scheduler, window gather,
+BF16 tensor-core UNets, blend/update/re-noise and decode all run per step.
+Weights are seeded random-init (synthetic data); every step queries a fresh
+location with an emptied tile cache, so nothing is reused across steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl idf|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank serves its
+own queries (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+QUERY = 4096
+METRIC = "final heightmap px/s, BF16/FP8+batched vs plain FP32 at stated error"
+WORKLOAD = ("2-level hierarchy (coarse 64/128/128 @1/8, fine 64/128/256/256 + attention), "
+            "128x128 windows stride 64, 20 steps, 4096x4096 metres query, BF16 convs")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="idf", choices=["idf", "reference"])
+    p.add_argument("--query", type=int, default=QUERY)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp32", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- workload
+
+def stack_and_weights():
+    import synth
+    st = synth.config2_stack()
+    # the library reports its own parameter layout; weights are drawn for it
+    import paper_2512_08309_gb300 as idf
+    wts = [synth.weights(idf.param_shapes(lv), 0, i) for i, lv in enumerate(st["level"])]
+    return st, wts
+
+
+def window_counts(st, q):
+    """Windows a cold metres query of a q x q region evaluates per level
+    (cone of the decode rect; coarse cone covers the fine conditioning)."""
+    import paper_2512_08309_gb300 as idf
+    Lr, Hr = idf.laplacian_halo(st, 0, 0, q, q)
+    fine, coarse = st["level"][1], st["level"][0]
+
+    def cone(x0, y0, w, h, lv):
+        s, H, K = lv["stride"], lv["window"], lv["steps"]
+        r = H // s
+        ty0, tx0 = y0 // s, x0 // s
+        ty1, tx1 = (y0 + h - 1) // s, (x0 + w - 1) // s
+        n = 0
+        wins = None
+        for _ in range(K):
+            wy0, wx0, wy1, wx1 = ty0 - (r - 1), tx0 - (r - 1), ty1, tx1
+            n += (wy1 - wy0 + 1) * (wx1 - wx0 + 1)
+            wins = (wy0, wx0, wy1, wx1)
+            ty0, tx0, ty1, tx1 = wy0, wx0, wy1 + r - 1, wx1 + r - 1
+        return n, wins
+
+    nf, wins = cone(Hr[0], Hr[1], Hr[2], Hr[3], fine)
+    s, H, f = fine["stride"], fine["window"], fine["scale_to_parent"]
+    cy0, cx0 = (wins[0] * s) // f, (wins[1] * s) // f
+    cy1, cx1 = (wins[2] * s + H - 1) // f, (wins[3] * s + H - 1) // f
+    y0, x0 = min(cy0, Lr[1]), min(cx0, Lr[0])
+    y1, x1 = max(cy1, Lr[1] + Lr[3] - 1), max(cx1, Lr[0] + Lr[2] - 1)
+    nc, _ = cone(x0, y0, x1 - x0 + 1, y1 - y0 + 1, coarse)
+    return nf, nc
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle timing
+
+def oracle_sample(seconds=15.0):
+    """Time the FP64 oracle on a bounded sample of the workload: fine and coarse
+    window evaluations (Phi: UNet + preconditioning + re-noise), interleaved
+    in the workload's fine:coarse ratio, until `seconds` have passed.  Returns
+    (px/s estimate, description, threads)."""
+    import numpy as np
+
+    import synth
+    from oracle import sampler as OS
+    from oracle import unet as OU
+    st = synth.config2_stack()
+    wts = [synth.weights([s for _, s in OU.param_shapes(lv)], 0, i) for i, lv in enumerate(st["level"])]
+    nf, nc = window_counts(st, QUERY)
+    world = OS.World(0, st, wts)
+    fine, coarse = world.levels[1], world.levels[0]
+    # coarse result the fine conditioning reads: a constant stand-in avoids
+    # recursing into the coarse cone inside the timed fine evaluations
+    fine.cond = lambda y0, x0, h, w: np.zeros((h, w))
+    H = fine.H
+    t0 = time.perf_counter()
+    done_f = done_c = 0
+    i = 0
+    while True:
+        x = [np.random.default_rng(i).standard_normal((H, H)) * 80.0]
+        if done_c * nf < done_f * nc:
+            coarse.phi(0, x, [(0, i * 64, H, H)])
+            done_c += 1
+        else:
+            fine.phi(0, x, [(0, i * 64, H, H)])
+            done_f += 1
+        i += 1
+        if time.perf_counter() - t0 > seconds and done_f >= 1:
+            break
+    dt = time.perf_counter() - t0
+    # time per query = per-window times scaled to the cone's window counts
+    est = dt * (nf / max(done_f, 1))
+    if done_c:
+        # split the measured time in proportion to FLOPs of the windows done
+        ff = OU.flops_per_window(st["level"][1])
+        fc = OU.flops_per_window(st["level"][0])
+        tf = dt * done_f * ff / (done_f * ff + done_c * fc)
+        tc = dt - tf
+        est = tf / done_f * nf + tc / done_c * nc
+    px_s = QUERY * QUERY / est
+    desc = (f"FP64 NumPy oracle: {done_f} fine + {done_c} coarse 128x128 window evaluations "
+            f"in {dt:.1f} s, scaled to the {nf} fine + {nc} coarse windows of one cold "
+            f"{QUERY}x{QUERY} query")
+    threads = os.cpu_count()
+    return px_s, desc, threads, est
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cores = os.cpu_count()
+    vals = []
+    desc = None
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        px, desc, threads, _ = oracle_sample(seconds=10.0)
+        vals.append(px)
+    elapsed = time.perf_counter() - t_all
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "px/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * QUERY * QUERY / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "query": QUERY},
+        "cpu_baseline": {"value": v, "unit": "px/s", "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": elapsed,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- idf arm
+
+def traffic_record():
+    """Per-launch DRAM traffic of the tensor-core conv from a committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "conv_tc_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_2512_08309_gb300", "csrc", "conv_tc.cu"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_idf(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_2512_08309_gb300 as idf
+    idf.lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    st, wts = stack_and_weights()
+    q = args.query
+    W = idf.World(0, st, wts, precision="bf16", device=local, profile=True)
+    out = torch.empty((q, q), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def loc(i):
+        # distinct far-apart locations per rank and step; nothing is reused
+        return (rank * 7919 + i) * (1 << 22) - (1 << 30), ((rank * 104729 + 3 * i) % 1000) * (1 << 21)
+
+    def step(i):
+        W.cache_clear()
+        x0, y0 = loc(i)
+        W.query_device(x0, y0, q, q, out.data_ptr(), q, kind=idf.IDF_OUT_METRES, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    s0 = W.stats()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/idf_clocks_{rank}.csv")
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop(local)
+    ms = e0.elapsed_time(e1)
+    s1 = W.stats()
+    ms = max_over_ranks(ms, world)
+    ms_step = ms / args.steps
+    value = world * q * q * args.steps / (ms / 1000.0)
+    finite = bool(torch.isfinite(out).all().item())
+
+    prof = {}
+    for k in s1["profile"]:
+        a, b = s0["profile"][k], s1["profile"][k]
+        prof[k] = {f: b[f] - a[f] for f in ("launches", "ms", "flops", "bytes")}
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    wins = [b["windows_evaluated"] - a["windows_evaluated"] for a, b in zip(s0["levels"], s1["levels"])]
+
+    pk, pk_kind = peaks()
+    tc = prof["conv_tc"]
+    achieved = tc["flops"] / (tc["ms"] / 1000.0) / 1e12 if tc["ms"] > 0 else 0.0
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    rec = traffic_record()
+    roofline = {"kernel": "conv_tc (tcgen05 implicit-GEMM conv)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_kind": f"{pk_kind} bf16 sustained",
+                "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                "algorithmic_bytes_per_launch": tc["bytes"] / max(1, tc["launches"]),
+                "flops_per_launch": tc["flops"] / max(1, tc["launches"]),
+                "avg_launch_ms": tc["ms"] / max(1, tc["launches"]),
+                "share_of_step": tc["ms"] / ms if ms > 0 else None}
+    hbm = {}
+    for k in ("blend", "decode", "groupnorm", "gather"):
+        p = prof[k]
+        if p["ms"] > 0:
+            gbs = p["bytes"] / (p["ms"] / 1000.0) / 1e9
+            hbm[k] = {"achieved_gbs": gbs, "frac": gbs / pk["hbm_gbs"], "launches": p["launches"],
+                      "share_of_step": p["ms"] / ms}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "query": q, "steps_per_level": 20, "precision": "bf16",
+                   "windows_per_step": {"coarse": wins[0] / args.steps, "fine": wins[1] / args.steps},
+                   "cache": "emptied every step; working set of several GB per step exceeds L2",
+                   "parallelism": f"{world} independent worlds" if world > 1 else "single GPU"},
+        "gpu_launches": launches, "output_finite": finite,
+        "roofline": roofline, "hbm_kernels": hbm,
+        "kernel_ms": {k: v["ms"] for k, v in prof.items() if v["launches"]},
+        "clocks": clk,
+    }
+
+    # end to end through the public host-buffer call (D2H inside the timed region)
+    if not args.no_e2e:
+        host = np.empty((q, q), dtype=np.float32)
+        W.cache_clear()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        n_e2e = max(1, args.steps)
+        for i in range(n_e2e):
+            W.cache_clear()
+            x0, y0 = loc(1000 + i)
+            W.query(x0, y0, q, q, kind=idf.IDF_OUT_METRES, out=host)
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        line["e2e"] = {"value": world * q * q * n_e2e / dt, "unit": "px/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": q * q * 4, "steps": n_e2e}
+    W.close()
+
+    # the plain FP32 sampler's network and the BF16 one, windows/s through
+    # idf_unet_forward, converted to this workload's px/s (UNets dominate)
+    if not args.no_fp32 and rank == 0:
+        nf, nc = window_counts(st, q)
+        res = {}
+        for prec, nb in (("fp32", 8), ("bf16", 64)):
+            Wp = idf.World(0, st, wts, precision=prec, max_batch=nb)
+            t_lv = []
+            for li, n_win in ((1, nb), (0, nb)):
+                H = st["level"][li]["window"]
+                x = torch.randn((n_win, st["level"][li]["in_ch"], H, H), device=dev)
+                y = torch.empty((n_win, 1, H, H), device=dev)
+                Wp.unet_forward(li, x.data_ptr(), n_win, y.data_ptr(), stream=stream)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                Wp.unet_forward(li, x.data_ptr(), n_win, y.data_ptr(), stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t_lv.append(a.elapsed_time(b) / 1000.0 / n_win)
+            Wp.close()
+            t_query = t_lv[0] * nf + t_lv[1] * nc
+            res[prec] = {"px_s": q * q / t_query, "fine_window_ms": 1000 * t_lv[0],
+                         "coarse_window_ms": 1000 * t_lv[1], "batch": nb}
+        line["plain_fp32"] = {"value": res["fp32"]["px_s"], "unit": "px/s",
+                              "method": "FP32 SIMT UNet windows/s (idf_unet_forward) x windows per "
+                                        "final px of this workload",
+                              "bf16_same_method": res["bf16"]["px_s"],
+                              "speedup_bf16_vs_fp32_unet": res["bf16"]["px_s"] / res["fp32"]["px_s"],
+                              "detail": res}
+    if not args.no_cpu and rank == 0 and world == 1:
+        px, desc, threads, est = oracle_sample(seconds=15.0)
+        line["cpu_baseline"] = {"value": px, "unit": "px/s", "cores": threads, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_idf(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * idf.h -- C ABI of libidf, a GB300 (sm_103a) implementation of
+ * InfiniteDiffusion sampling (arXiv 2512.08309) over an unbounded 2-D canvas.
+ *
+ * The library answers region queries J_0[R] of the paper's lazily evaluated
+ * infinite image (Sec. 3.2-3.3, Eq. 2, Alg. 1): a seed fixes the whole world
+ * (Sec. 3.5 "Seed consistency", App. B "Seeds and initial noise"), any
+ * rectangle can be queried in any order at constant cost (Sec. 3.5
+ * "Constant-time random access", Thm 2), and a model stack may chain a coarse
+ * level into a fine one (App. C.3 "Dependency chaining", Sec. 5.3) whose pair
+ * of outputs is decoded from the Laplacian encoding into metres (Sec. 5.2,
+ * App. H).
+ *
+ * Conventions shared by every call
+ *   - Coordinates are absolute pixel indices on Z^2; x is the column axis
+ *     (the paper's second window index j), y the row axis.  Outputs are
+ *     row-major: out[r * pitch + c] holds pixel (x0 + c, y0 + r).
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps (weights, descriptors) and owns the world, its tile cache, its
+ *     device workspace and its CUDA stream.
+ *   - Every call returns an idf_status; nothing aborts and no C++ exception
+ *     crosses the ABI.  idf_world_last_error() gives a message.
+ *   - After IDF_ECUDA or IDF_ETIMEOUT a world refuses further queries with
+ *     IDF_EINTERNAL; destroy it and create a new one.
+ *   - A world is not thread-safe: one host thread per world.
+ *   - Identical (seed, stack, opts) give bitwise identical results whatever
+ *     the query order, the batching of queries or the cache size.
+ */
+#ifndef IDF_H_
+#define IDF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idf_world idf_world;
+
+typedef enum {
+  IDF_OK = 0,
+  IDF_EINVAL = 1,        /* bad argument or descriptor */
+  IDF_ENOMEM = 2,        /* device or host allocation failed, or cache too small */
+  IDF_ECUDA = 3,         /* a CUDA call failed; the world is unusable afterwards */
+  IDF_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+  IDF_EMODEL = 5,        /* weights do not match the described network */
+  IDF_EDEVICE_CHECK = 6, /* a device-side bounds check fired */
+  IDF_EINTERNAL = 7,     /* world poisoned by an earlier failure, or a bug */
+  IDF_EUNSUPPORTED = 8   /* valid request that this build does not implement */
+} idf_status;
+
+typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2 } idf_precision;
+
+typedef enum {
+  IDF_OUT_MODEL = 0,  /* the last level's final sample J_K in model units */
+  IDF_OUT_METRES = 1  /* Laplacian decode of (coarse, fine) to metres (stacks with laplacian=1) */
+} idf_output_kind;
+
+/*
+ * One level of the model stack: a window denoiser Phi and its sliding-window
+ * layout (Sec. 3.2: window (i,j) covers rows [i*stride, i*stride+window) and
+ * columns [j*stride, j*stride+window)).  window must be a multiple of stride
+ * (r = window/stride windows cover each stride x stride tile per axis) and
+ * offset must be 0.
+ *
+ * The denoiser (test_denoiser = 0) is the ResBlock UNet described in
+ * idf_model_param_shape(); it is EDM-preconditioned:
+ *   D(x; sigma) = c_skip x + c_out F(c_in x [, conditioning]).
+ * steps = K blended sampler steps on the rho-schedule from sigma_max to
+ * sigma_min.  scale_to_parent = f > 0 makes the level conditioned on the
+ * previous level of the stack: input channel 1 is that level's result
+ * upsampled (nearest) by f (Sec. 5.3).  test_denoiser 1/2/3 replace F by a
+ * closed-form function (constant 0.5 / sum of input channels / sum of input
+ * channels + u/H - 2v/H in window-local row u and column v) for tests.
+ */
+typedef struct {
+  int32_t levels;            /* UNet resolution levels L >= 1 */
+  const int32_t* channels;   /* L channel counts (host, copied) */
+  int32_t in_ch, out_ch;     /* in_ch = 1, or 2 with scale_to_parent > 0; out_ch = 1 */
+  int32_t gn_groups;         /* GroupNorm groups (divides every channel count) */
+  int32_t attn_at_bottom;    /* 1: self-attention block before the bottom ResBlock */
+  int32_t attn_heads;        /* heads of that block (divides channels[L-1]) */
+  const float* weights;      /* host, n_weights floats in declaration order (copied) */
+  size_t n_weights;
+  int32_t window, stride, offset, steps;
+  double sigma_max, sigma_min, rho, sigma_data;
+  int32_t scale_to_parent;   /* 0 for the first level; 8 for fine-under-coarse */
+  int32_t test_denoiser;     /* 0 = UNet */
+} idf_level_desc;
+
+/*
+ * A chain of levels, coarse first (at most 2).  laplacian = 1 (two levels)
+ * reads level 0 as the normalised low band L and level 1 as the normalised
+ * residual H of the Laplacian encoding (Sec. 5.2) and enables
+ * IDF_OUT_METRES: l = low_mu + low_scale L, h = res_scale H,
+ * P = up(l) + h, l^ = blur(down(P)), v = up(l^) + h, metres = sign(v) v^2
+ * (App. H), with down = mean over lap_factor^2 blocks, blur = Gaussian of
+ * lap_blur_sigma low-res pixels truncated at lap_radius, up = bilinear with
+ * half-pixel centres.  blend_eps is the weight at a window's border
+ * (Sec. 6: separable linear window, 1 at the centre).
+ */
+typedef struct {
+  int32_t n_levels;
+  const idf_level_desc* level;
+  int32_t laplacian;
+  int32_t lap_factor;
+  double lap_blur_sigma;
+  int32_t lap_radius;
+  double low_mu, low_scale, res_scale;
+  double blend_eps;
+} idf_model_stack;
+
+typedef struct {
+  idf_precision precision;          /* arithmetic of the UNet convolutions */
+  size_t cache_bytes;               /* device tile cache; 0 = default (8 GiB) */
+  int32_t device;                   /* CUDA device ordinal */
+  size_t workspace_bytes;           /* UNet activation workspace; 0 = default */
+  int32_t max_batch;                /* windows per UNet launch; 0 = from workspace */
+  int32_t profile;                  /* 1: time every kernel launch with CUDA events on the
+                                       world's stream; per-class totals in idf_world_stats */
+} idf_world_opts;
+
+typedef struct {
+  int64_t x0, y0;
+  int32_t w, h;
+  float* out_dev;                   /* device, caller-owned, h rows of pitch_elems */
+  int64_t pitch_elems;
+} idf_region;
+
+/* ---------------------------------------------------------------- worlds */
+
+/* Create a world: validates the stack, copies weights to the device (and
+ * packs BF16 copies when precision = IDF_BF16), computes the sigma schedule,
+ * preconditioning coefficients, blend table and blur taps in FP64 on the
+ * host, and allocates the tile cache.  *out is NULL on failure. */
+idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack,
+                            const idf_world_opts* opts, idf_world** out);
+
+/* Query J_K (or metres) over [x0, x0+w) x [y0, y0+h) into a host buffer of
+ * w*h floats (row-major, caller-owned).  w, h >= 1, w*h <= 2^31, and every
+ * tile index must fit in int32.  Blocks until the result is on the host. */
+idf_status idf_world_query(idf_world* world, int64_t x0, int64_t y0, int32_t w, int32_t h,
+                           idf_output_kind kind, float* out_host);
+
+/* Same, writing into device memory (h rows of pitch_elems >= w floats) on
+ * the caller's CUDA stream (NULL = legacy default stream).  The world's own
+ * stream is joined to it before and after; returns once the work is queued. */
+idf_status idf_world_query_device(idf_world* world, int64_t x0, int64_t y0, int32_t w,
+                                  int32_t h, idf_output_kind kind, float* out_dev,
+                                  int64_t pitch_elems, void* cuda_stream);
+
+/* Serve n regions as one batch: the window evaluations of all regions at
+ * each step share launches (Thm 3: T - t rounds for any finite query set).
+ * Results are bitwise identical to serving the regions one by one. */
+idf_status idf_world_query_batch(idf_world* world, const idf_region* regions, int32_t n,
+                                 idf_output_kind kind, void* cuda_stream);
+
+/* Drop every cached tile (Sec. 3.3: eviction makes windows unprocessed). */
+idf_status idf_world_cache_clear(idf_world* world);
+
+/* JSON object with counters: windows evaluated per level, tiles computed,
+ * cache hits / misses / evictions, kernel launches, bytes of the cache, and
+ * (with opts.profile) per kernel class the launches, device milliseconds and
+ * algorithmic FLOPs / bytes.  Synchronizes the world's stream. */
+idf_status idf_world_stats(const idf_world* world, char* json_buf, size_t buf_len);
+
+/* Message of the last failure on this world; valid until the next call. */
+const char* idf_world_last_error(const idf_world* world);
+
+/* Release everything the world owns; NULL-safe. */
+void idf_world_destroy(idf_world* world);
+
+/* Window indices (i = row, j = column) that a query of the region with the
+ * current cache evaluates at step `step` (0 = first denoising step) of a
+ * level: kappa of the missing tiles (Alg. 3) applied recursively as in
+ * Alg. 1.  Writes up to cap pairs (i, j) into win_ij and the total count
+ * into *n_out.  Does not evaluate anything. */
+idf_status idf_debug_cone(idf_world* world, int64_t x0, int64_t y0, int32_t w, int32_t h,
+                          int32_t level, int32_t step, int64_t* win_ij, int32_t cap,
+                          int32_t* n_out);
+
+/* --------------------------------------------------------- building blocks */
+
+/* The seed function G (App. B): N(seed, level, step, x, y), standard normal
+ * in binary32, defined bit for bit by Philox4x32-10 (key = seed, counter =
+ * (x mod 2^32, y mod 2^32, step, level)) and Box-Muller with the library's
+ * own binary32 polynomials for ln and cos.  Writes h rows of w values at
+ * out_dev (pitch_elems floats per row) on the given stream. */
+idf_status idf_noise_fill(uint64_t seed, uint32_t level, uint32_t step, int64_t x0, int64_t y0,
+                          int32_t w, int32_t h, float* out_dev, int64_t pitch_elems,
+                          void* cuda_stream);
+
+/* Number of weight tensors of a level's UNet and the shape (C_out, C_in,
+ * kh, kw) of tensor `index` in declaration order: in_conv; per encoder level
+ * conv1, conv2, [1x1 skip when channels change]; [attention qkv (3C, C, 1, 1),
+ * proj (C, C, 1, 1)]; bottom ResBlock; per decoder level (deepest first)
+ * conv1, conv2, skip; out_conv. */
+idf_status idf_model_param_count(const idf_level_desc* level, int32_t* n_tensors,
+                                 size_t* n_weights);
+idf_status idf_model_param_shape(const idf_level_desc* level, int32_t index, int32_t shape[4]);
+
+/* Phi's network F (Sec. 5.3, the UNet of a level) on a batch of windows:
+ * x_dev (n, in_ch, window, window) float32 NCHW, y_dev (n, out_ch, window,
+ * window) float32, both device.  Runs in the world's precision. */
+idf_status idf_unet_forward(idf_world* world, int32_t level, const float* x_dev, int32_t n,
+                            float* y_dev, void* cuda_stream);
+
+/* Laplacian denoising decode (Sec. 5.2, App. H) of explicit bands: L_dev is
+ * the normalised low band on the coarse grid, origin (lx0, ly0), lw x lh,
+ * pitch lpitch; H_dev the normalised residual on the fine grid, origin (hx0,
+ * hy0), hw x hh, pitch hpitch.  Writes metres for [x0, x0+w) x [y0, y0+h)
+ * into out_dev.  The bands must cover the rects idf_laplacian_halo()
+ * returns for the query (IDF_EINVAL otherwise); about (lap_radius + 1) *
+ * lap_factor fine pixels of H and lap_radius + 2 coarse pixels of L on each
+ * side. */
+idf_status idf_laplacian_decode(const idf_model_stack* stack, const float* L_dev, int64_t lx0,
+                                int64_t ly0, int32_t lw, int32_t lh, int64_t lpitch,
+                                const float* H_dev, int64_t hx0, int64_t hy0, int32_t hw,
+                                int32_t hh, int64_t hpitch, int64_t x0, int64_t y0, int32_t w,
+                                int32_t h, float* out_dev, int64_t pitch_elems,
+                                void* cuda_stream);
+
+/* Halo the decode of [x0, x0+w) x [y0, y0+h) reads: the coarse rect of L and
+ * the fine rect of H, each as (x0, y0, w, h). */
+idf_status idf_laplacian_halo(const idf_model_stack* stack, int64_t x0, int64_t y0, int32_t w,
+                              int32_t h, int64_t L_rect[4], int64_t H_rect[4]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDF_H_ */

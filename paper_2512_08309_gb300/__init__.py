@@ -1,0 +1,302 @@
+"""GB300 implementation of InfiniteDiffusion sampling (arXiv 2512.08309).
+
+A thin ctypes binding over libidf (include/idf.h): argument marshalling only,
+every step of the sampling path runs in the library's CUDA kernels.  The
+library is built in-tree by ``paper_2512_08309_gb300.build.build()``; if it
+is missing, every call raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libidf.so")
+
+IDF_OK, IDF_EINVAL, IDF_ENOMEM, IDF_ECUDA, IDF_ETIMEOUT, IDF_EMODEL, IDF_EDEVICE_CHECK, \
+    IDF_EINTERNAL, IDF_EUNSUPPORTED = range(9)
+STATUS_NAMES = ["IDF_OK", "IDF_EINVAL", "IDF_ENOMEM", "IDF_ECUDA", "IDF_ETIMEOUT", "IDF_EMODEL",
+                "IDF_EDEVICE_CHECK", "IDF_EINTERNAL", "IDF_EUNSUPPORTED"]
+IDF_FP32, IDF_BF16, IDF_FP8_E4M3 = 0, 1, 2
+IDF_OUT_MODEL, IDF_OUT_METRES = 0, 1
+
+PRECISIONS = {"fp32": IDF_FP32, "bf16": IDF_BF16, "fp8": IDF_FP8_E4M3}
+
+# Every symbol include/idf.h declares.
+EXPORTS = [
+    "idf_world_create", "idf_world_query", "idf_world_query_device", "idf_world_query_batch",
+    "idf_world_cache_clear", "idf_world_stats", "idf_world_last_error", "idf_world_destroy",
+    "idf_debug_cone", "idf_noise_fill", "idf_model_param_count", "idf_model_param_shape",
+    "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo",
+]
+
+
+class IdfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+
+
+class idf_level_desc(C.Structure):
+    _fields_ = [
+        ("levels", C.c_int32), ("channels", C.POINTER(C.c_int32)),
+        ("in_ch", C.c_int32), ("out_ch", C.c_int32), ("gn_groups", C.c_int32),
+        ("attn_at_bottom", C.c_int32), ("attn_heads", C.c_int32),
+        ("weights", C.POINTER(C.c_float)), ("n_weights", C.c_size_t),
+        ("window", C.c_int32), ("stride", C.c_int32), ("offset", C.c_int32), ("steps", C.c_int32),
+        ("sigma_max", C.c_double), ("sigma_min", C.c_double), ("rho", C.c_double),
+        ("sigma_data", C.c_double),
+        ("scale_to_parent", C.c_int32), ("test_denoiser", C.c_int32),
+    ]
+
+
+class idf_model_stack(C.Structure):
+    _fields_ = [
+        ("n_levels", C.c_int32), ("level", C.POINTER(idf_level_desc)),
+        ("laplacian", C.c_int32), ("lap_factor", C.c_int32), ("lap_blur_sigma", C.c_double),
+        ("lap_radius", C.c_int32), ("low_mu", C.c_double), ("low_scale", C.c_double),
+        ("res_scale", C.c_double), ("blend_eps", C.c_double),
+    ]
+
+
+class idf_world_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("cache_bytes", C.c_size_t), ("device", C.c_int32),
+        ("workspace_bytes", C.c_size_t), ("max_batch", C.c_int32), ("profile", C.c_int32),
+    ]
+
+
+class idf_region(C.Structure):
+    _fields_ = [("x0", C.c_int64), ("y0", C.c_int64), ("w", C.c_int32), ("h", C.c_int32),
+                ("out_dev", C.c_void_p), ("pitch_elems", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libidf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libidf is not built ({LIB_PATH} missing); run "
+                           "paper_2512_08309_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_uint32
+    fp = C.POINTER(C.c_float)
+    sig = {
+        "idf_world_create": ([u64, C.POINTER(idf_model_stack), C.POINTER(idf_world_opts), C.POINTER(vp)], i32),
+        "idf_world_query": ([vp, i64, i64, i32, i32, i32, vp], i32),
+        "idf_world_query_device": ([vp, i64, i64, i32, i32, i32, vp, i64, vp], i32),
+        "idf_world_query_batch": ([vp, C.POINTER(idf_region), i32, i32, vp], i32),
+        "idf_world_cache_clear": ([vp], i32),
+        "idf_world_stats": ([vp, C.c_char_p, C.c_size_t], i32),
+        "idf_world_last_error": ([vp], C.c_char_p),
+        "idf_world_destroy": ([vp], None),
+        "idf_debug_cone": ([vp, i64, i64, i32, i32, i32, i32, C.POINTER(i64), i32, C.POINTER(i32)], i32),
+        "idf_noise_fill": ([u64, u32, u32, i64, i64, i32, i32, vp, i64, vp], i32),
+        "idf_model_param_count": ([C.POINTER(idf_level_desc), C.POINTER(i32), C.POINTER(C.c_size_t)], i32),
+        "idf_model_param_shape": ([C.POINTER(idf_level_desc), i32, C.POINTER(i32)], i32),
+        "idf_unet_forward": ([vp, i32, vp, i32, vp, vp], i32),
+        "idf_laplacian_decode": ([C.POINTER(idf_model_stack), vp, i64, i64, i32, i32, i64, vp, i64, i64,
+                                  i32, i32, i64, i64, i64, i32, i32, vp, i64, vp], i32),
+        "idf_laplacian_halo": ([C.POINTER(idf_model_stack), i64, i64, i32, i32, C.POINTER(i64),
+                                C.POINTER(i64)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+# --------------------------------------------------------------- descriptors
+
+class _Keep:
+    """Holds the ctypes arrays a descriptor points into."""
+
+    def __init__(self):
+        self.refs = []
+
+
+def level_desc(lv: dict, weights=None, keep: Optional[_Keep] = None) -> idf_level_desc:
+    import numpy as np
+    keep = keep or _Keep()
+    ch = (C.c_int32 * len(lv["channels"]))(*lv["channels"])
+    keep.refs.append(ch)
+    d = idf_level_desc()
+    d.levels = lv["levels"]
+    d.channels = ch
+    d.in_ch, d.out_ch, d.gn_groups = lv["in_ch"], lv["out_ch"], lv["gn_groups"]
+    d.attn_at_bottom, d.attn_heads = lv["attn_at_bottom"], lv["attn_heads"]
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        keep.refs.append(w)
+        d.weights = w.ctypes.data_as(C.POINTER(C.c_float))
+        d.n_weights = w.size
+    d.window, d.stride, d.offset, d.steps = lv["window"], lv["stride"], lv["offset"], lv["steps"]
+    d.sigma_max, d.sigma_min, d.rho, d.sigma_data = lv["sigma_max"], lv["sigma_min"], lv["rho"], lv["sigma_data"]
+    d.scale_to_parent, d.test_denoiser = lv["scale_to_parent"], lv["test_denoiser"]
+    return d
+
+
+def model_stack(st: dict, weights: Optional[Sequence] = None, keep: Optional[_Keep] = None) -> idf_model_stack:
+    keep = keep or _Keep()
+    n = len(st["level"])
+    arr = (idf_level_desc * n)()
+    for i, lv in enumerate(st["level"]):
+        arr[i] = level_desc(lv, None if weights is None else weights[i], keep)
+    keep.refs.append(arr)
+    s = idf_model_stack()
+    s.n_levels = n
+    s.level = arr
+    s.laplacian, s.lap_factor, s.lap_blur_sigma, s.lap_radius = (
+        st["laplacian"], st["lap_factor"], st["lap_blur_sigma"], st["lap_radius"])
+    s.low_mu, s.low_scale, s.res_scale, s.blend_eps = st["low_mu"], st["low_scale"], st["res_scale"], st["blend_eps"]
+    keep.refs.append(s)
+    return s
+
+
+def param_shapes(lv: dict):
+    """[(C_out, C_in, kh, kw)] of a level's UNet, in the library's declaration order."""
+    L = lib()
+    keep = _Keep()
+    d = level_desc(lv, None, keep)
+    nt, nw = C.c_int32(), C.c_size_t()
+    _check(L.idf_model_param_count(C.byref(d), C.byref(nt), C.byref(nw)), "param count")
+    out = []
+    for i in range(nt.value):
+        s = (C.c_int32 * 4)()
+        _check(L.idf_model_param_shape(C.byref(d), i, s), "param shape")
+        out.append(tuple(s))
+    return out
+
+
+def _check(status: int, what: str, world=None):
+    if status != IDF_OK:
+        msg = what
+        if world is not None:
+            m = lib().idf_world_last_error(world)
+            msg = f"{what}: {m.decode() if m else ''}"
+        raise IdfError(status, msg)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class World:
+    """idf_world: a seeded infinite canvas of one model stack."""
+
+    def __init__(self, seed: int, stack: dict, weights: Optional[Sequence] = None,
+                 precision: str = "fp32", cache_bytes: int = 0, device: int = 0,
+                 workspace_bytes: int = 0, max_batch: int = 0, profile: bool = False):
+        L = lib()
+        self._keep = _Keep()
+        self.stack = stack
+        st = model_stack(stack, weights, self._keep)
+        o = idf_world_opts()
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.cache_bytes, o.device, o.workspace_bytes, o.max_batch = cache_bytes, device, workspace_bytes, max_batch
+        o.profile = 1 if profile else 0
+        h = C.c_void_p()
+        _check(L.idf_world_create(C.c_uint64(seed), C.byref(st), C.byref(o), C.byref(h)), "idf_world_create")
+        self._h = h
+        self._stack_c = st
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().idf_world_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, x0: int, y0: int, w: int, h: int, kind: int = IDF_OUT_MODEL, out=None):
+        """idf_world_query into a host float32 array (h, w)."""
+        import numpy as np
+        if out is None:
+            out = np.empty((h, w), dtype=np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size >= w * h
+        _check(lib().idf_world_query(self._h, x0, y0, w, h, kind, out.ctypes.data_as(C.c_void_p)),
+               "idf_world_query", self._h)
+        return out
+
+    def query_device(self, x0: int, y0: int, w: int, h: int, out_ptr: int, pitch: int,
+                     kind: int = IDF_OUT_MODEL, stream=None):
+        """idf_world_query_device into device memory (e.g. a torch tensor's data_ptr())."""
+        _check(lib().idf_world_query_device(self._h, x0, y0, w, h, kind, C.c_void_p(out_ptr), pitch,
+                                            _stream_ptr(stream)), "idf_world_query_device", self._h)
+
+    def query_batch(self, regions, kind: int = IDF_OUT_MODEL, stream=None):
+        """regions: [(x0, y0, w, h, out_ptr, pitch)]"""
+        arr = (idf_region * len(regions))()
+        for i, (x0, y0, w, h, p, pitch) in enumerate(regions):
+            arr[i] = idf_region(x0, y0, w, h, p, pitch)
+        _check(lib().idf_world_query_batch(self._h, arr, len(regions), kind, _stream_ptr(stream)),
+               "idf_world_query_batch", self._h)
+
+    def cache_clear(self):
+        _check(lib().idf_world_cache_clear(self._h), "idf_world_cache_clear", self._h)
+
+    def stats(self) -> dict:
+        buf = C.create_string_buffer(1 << 16)
+        _check(lib().idf_world_stats(self._h, buf, len(buf)), "idf_world_stats", self._h)
+        return json.loads(buf.value.decode())
+
+    def last_error(self) -> str:
+        m = lib().idf_world_last_error(self._h)
+        return m.decode() if m else ""
+
+    def debug_cone(self, x0: int, y0: int, w: int, h: int, level: int, step: int):
+        n = C.c_int32()
+        _check(lib().idf_debug_cone(self._h, x0, y0, w, h, level, step, None, 0, C.byref(n)),
+               "idf_debug_cone", self._h)
+        buf = (C.c_int64 * (2 * max(1, n.value)))()
+        _check(lib().idf_debug_cone(self._h, x0, y0, w, h, level, step, buf, n.value, C.byref(n)),
+               "idf_debug_cone", self._h)
+        return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+    def unet_forward(self, level: int, x_ptr: int, n: int, y_ptr: int, stream=None):
+        _check(lib().idf_unet_forward(self._h, level, C.c_void_p(x_ptr), n, C.c_void_p(y_ptr),
+                                      _stream_ptr(stream)), "idf_unet_forward", self._h)
+
+
+def noise_fill(seed: int, level: int, step: int, x0: int, y0: int, w: int, h: int, out_ptr: int,
+               pitch: int, stream=None):
+    _check(lib().idf_noise_fill(C.c_uint64(seed), level, step, x0, y0, w, h, C.c_void_p(out_ptr), pitch,
+                                _stream_ptr(stream)), "idf_noise_fill")
+
+
+def laplacian_halo(stack: dict, x0: int, y0: int, w: int, h: int):
+    keep = _Keep()
+    st = model_stack(stack, None, keep)
+    Lr, Hr = (C.c_int64 * 4)(), (C.c_int64 * 4)()
+    _check(lib().idf_laplacian_halo(C.byref(st), x0, y0, w, h, Lr, Hr), "idf_laplacian_halo")
+    return tuple(Lr), tuple(Hr)
+
+
+def laplacian_decode(stack: dict, L_ptr: int, lrect, lpitch: int, H_ptr: int, hrect, hpitch: int,
+                     x0: int, y0: int, w: int, h: int, out_ptr: int, pitch: int, stream=None):
+    """lrect / hrect = (x0, y0, w, h) of the bands on their own grids."""
+    keep = _Keep()
+    st = model_stack(stack, None, keep)
+    _check(lib().idf_laplacian_decode(C.byref(st), C.c_void_p(L_ptr), lrect[0], lrect[1], lrect[2], lrect[3],
+                                      lpitch, C.c_void_p(H_ptr), hrect[0], hrect[1], hrect[2], hrect[3], hpitch,
+                                      x0, y0, w, h, C.c_void_p(out_ptr), pitch, _stream_ptr(stream)),
+           "idf_laplacian_decode")

@@ -1,0 +1,399 @@
+// Implicit-GEMM convolution on the sm_103a tensor cores (tcgen05 + TMEM),
+// fed by TMA.  This is the dense contraction of the window denoiser F
+// (Sec. 5.3): a 3x3 (or 1x1) zero-padded convolution of bfloat16 NHWC
+// activations with bfloat16 weights, accumulated in float32 in tensor memory.
+//
+//   GEMM view: M = pixels of a window batch, N = C_out, K = taps * C_in.
+//   CTA tile:  128 pixels (whole rows of one window) x BN output channels.
+//   K stage:   one tap (dy, dx) and 64 input channels: a 4-D TMA box of the
+//              activation tensor (64 channels x W x 128/W rows x 1 window)
+//              at the tap's offset -- out-of-range rows and columns are
+//              zero-filled by TMA, which is exactly the window's zero padding
+//              -- and a 2-D TMA box of the weights (64 channels x BN rows).
+//              Both land in shared memory in the 128-byte swizzled K-major
+//              layout that the UMMA descriptors describe.
+//   Warps:     warp 0 lane 0 issues TMA; warp 1 allocates TMEM and lane 0
+//              issues tcgen05.mma (M=128, N=BN, K=16, four per stage) and
+//              tcgen05.commit; warps 2-5 wait for the accumulator, read it
+//              with tcgen05.ld (warp w reads TMEM lanes 32*(w%4)..+31) and
+//              write float32 NHWC output, adding the residual if given.
+//   Waits:     every mbarrier wait is bounded (clock64 budget); on expiry
+//              the CTA sets the status word, drains what it issued and
+//              frees its TMEM before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+
+#include "internal.h"
+
+namespace idf {
+namespace {
+
+constexpr int BM = 128;
+constexpr long long WAIT_LIMIT = 1000000000LL;  // clock64 cycles, about 0.5 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait.  honour_abort: give up as soon as another role aborted.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                         int* status, bool honour_abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (honour_abort && *abort_flag) return false;
+    if (clock64() - t0 > WAIT_LIMIT) {
+      atomicExch(status, 1);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
+// swizzle, 8-row core-matrix groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 x bf16 -> f32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcParams {
+  const float* res;
+  float* y;
+  int* status;
+  int H, W, Cout, ks, n_kc, n_iter;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB,
+                                                      TcParams p) {
+  constexpr int A_BYTES = BM * 128;
+  constexpr int B_BYTES = BN * 128;
+  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  uint8_t* smem = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
+  volatile int* abort_flag = &abort_sh;
+  // once any CTA of any launch has given up on a wait, later CTAs return at
+  // once (one thread reads the status so that the whole CTA decides alike)
+  __shared__ int skip_sh;
+  if (threadIdx.x == 0) skip_sh = *(volatile int*)p.status;
+  __syncthreads();
+  if (skip_sh) return;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int64_t HW = (int64_t)p.H * p.W;
+  const int win = (int)(m0 / HW);
+  const int y0 = (int)((m0 % HW) / p.W);
+  const int pad = p.ks / 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int last_issue[STAGES];
+      for (int s = 0; s < STAGES; ++s) last_issue[s] = -1;
+      for (int it = 0; it < p.n_iter; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true)) break;
+        const int tap = it / p.n_kc, kc = it % p.n_kc;
+        const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
+        uint8_t* a = smem + (size_t)s * STAGE_BYTES;
+        uint8_t* b = a + A_BYTES;
+        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        tma_load_4d(a, &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
+        tma_load_2d(b, &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
+        last_issue[s] = it;
+      }
+      if (*abort_flag) {
+        // drain the copies this thread issued before leaving
+        for (int s = 0; s < STAGES; ++s)
+          if (last_issue[s] >= 0)
+            wait_bar(&full_bar[s], (uint32_t)(last_issue[s] / STAGES) & 1u, abort_flag, p.status, false);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int it = 0; it < p.n_iter; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!wait_bar(&full_bar[s], ph, abort_flag, p.status, true)) break;
+        fence_after();
+        const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
+        const uint32_t b = a + A_BYTES;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16(tmem, umma_desc(a + 32 * k), umma_desc(b + 32 * k), idesc,
+                   (it > 0 || k > 0) ? 1u : 0u);
+        mma_commit(&empty_bar[s]);
+      }
+      mma_commit(&acc_bar);
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int64_t m = m0 + row;
+    if (wait_bar(&acc_bar, 0, abort_flag, p.status, true)) {
+      fence_after();
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        float* yp = p.y + m * p.Cout + n0 + c0;
+        const float* rp = p.res ? p.res + m * p.Cout + n0 + c0 : nullptr;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          if (rp) {
+            const float4 rv = reinterpret_cast<const float4*>(rp)[j];
+            v.x += rv.x; v.y += rv.y; v.z += rv.z; v.w += rv.w;
+          }
+          reinterpret_cast<float4*>(yp)[j] = v;
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (*abort_flag && lane == 0) {
+      // the last commit tracks every MMA issued; wait for it before freeing TMEM
+      wait_bar(&acc_bar, 0, abort_flag, p.status, false);
+    }
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+template <int BN, int STAGES>
+bool launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, dim3 grid, cudaStream_t st,
+            std::string* err) {
+  const size_t smem = (size_t)STAGES * (BM * 128 + BN * 128) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+      *err = "cudaFuncSetAttribute failed";
+      return false;
+    }
+    attr = true;
+  }
+  conv_tc_kernel<BN, STAGES><<<grid, 192, smem, st>>>(a, b, p);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+bool conv_tc_supported(int cin, int cout, int ks) {
+  return (ks == 1 || ks == 3) && cin >= 64 && cin % 64 == 0 && cout >= 64 && cout % 64 == 0 &&
+         (cout <= 256 || cout % 256 == 0);
+}
+
+bool conv_tc_shape_ok(int H, int W) {
+  return W >= 1 && W <= 128 && 128 % W == 0 && ((int64_t)H * W) % 128 == 0 && 128 / W <= H;
+}
+
+bool conv_tc_forward(const bf16* x, const bf16* w, const float* res, float* y, int n, int H, int W,
+                     int Cin, int Cout, int ks, int* status, cudaStream_t st, std::string* err) {
+  if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
+    *err = "shape not supported by the tensor-core convolution";
+    return false;
+  }
+  auto enc = encode_fn();
+  if (!enc) {
+    *err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const int BN = Cout <= 256 ? Cout : 256;
+  CUtensorMap ta, tb;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    cuuint32_t box[4] = {64, (cuuint32_t)W, (cuuint32_t)(128 / W), 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)x, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      *err = "tensor map (activations) encode failed";
+      return false;
+    }
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)ks * ks * Cout};
+    cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)BN};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)w, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      *err = "tensor map (weights) encode failed";
+      return false;
+    }
+  }
+  TcParams p;
+  p.res = res;
+  p.y = y;
+  p.status = status;
+  p.H = H;
+  p.W = W;
+  p.Cout = Cout;
+  p.ks = ks;
+  p.n_kc = Cin / 64;
+  p.n_iter = ks * ks * (Cin / 64);
+  const int64_t M = (int64_t)n * H * W;
+  dim3 grid((unsigned)(M / BM), (unsigned)(Cout / BN));
+  switch (BN) {
+    case 64: return launch<64, 4>(ta, tb, p, grid, st, err);
+    case 128: return launch<128, 3>(ta, tb, p, grid, st, err);
+    case 256: return launch<256, 2>(ta, tb, p, grid, st, err);
+    default:
+      *err = "unsupported N tile";
+      return false;
+  }
+}
+
+}  // namespace idf

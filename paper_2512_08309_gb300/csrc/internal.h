@@ -1,0 +1,188 @@
+// Internal declarations shared by the translation units of libidf.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace idf {
+
+typedef __nv_bfloat16 bf16;
+
+// Floor division and modulo for possibly negative numerators, positive d.
+__host__ __device__ __forceinline__ int64_t fdiv(int64_t a, int64_t d) {
+  int64_t q = a / d;
+  return (a % d != 0 && a < 0) ? q - 1 : q;
+}
+__host__ __device__ __forceinline__ int64_t fmod_pos(int64_t a, int64_t d) {
+  return a - fdiv(a, d) * d;
+}
+
+// ------------------------------------------------------------------ status
+struct Err {
+  int code = 0;  // idf_status
+  std::string msg;
+};
+
+// ---------------------------------------------------------------- sampler
+// A tile is stride x stride float32 values stored contiguously in one slot of
+// the tile pool.  slot < 0 means "not stored": the J_0 noise tile, computed on
+// the fly.
+struct GatherArgs {
+  const float* pool;         // tile pool base
+  const int32_t* win_slots;  // [n_win][r][r] slots of the tiles a window covers (row-major)
+  const int32_t* win_ij;     // [n_win][2] window indices (i row, j column)
+  int n_win, H, s, r, in_ch;
+  float c_in, sigma0;        // step-0 inputs are sigma0 * N(seed, level, 0, .)
+  int noise_step0;           // 1: inputs are the J_0 noise
+  uint64_t seed;
+  uint32_t level;
+  const float* cond;         // dense conditioning image (parent result) or null
+  int64_t cond_x0, cond_y0;  // its origin on the parent grid
+  int64_t cond_pitch;
+  int cond_w, cond_h, cond_f;
+  float* x_in;               // [n_win][H][H][in_ch] float32 (NHWC)
+  int* err_flag;             // device flag set on out-of-range reads
+};
+void launch_gather(const GatherArgs& a, cudaStream_t st);
+
+struct BlendArgs {
+  const float* pool;
+  float* pool_out;
+  const int32_t* tiles;      // [n_tiles][4]: ty, tx, slot_in (J_k, -1 for noise), slot_out
+  const int32_t* tile_wins;  // [n_tiles][r][r] batch index of window (ty-m, tx-n), m,n = 0..r-1
+  const float* F;            // [n_win][H][H] float32 network outputs
+  const float* w1;           // [H] blend weights per axis
+  const float* invB1;        // [s] 1 / per-axis weight sum
+  int n_tiles, H, s, r;
+  float c_skip, c_out, c_in, sigma_next, sigma0;
+  int noise_next;            // 1: add sigma_next N(seed, level, k+1, .)
+  int noise_in;              // 1: J_k is the J_0 noise (slot_in < 0)
+  uint32_t step_next;
+  uint64_t seed;
+  uint32_t level;
+};
+void launch_blend(const BlendArgs& a, cudaStream_t st);
+
+// Closed-form test denoisers on x_in (NHWC, in_ch channels) -> F [n][H][H].
+void launch_test_denoiser(int kind, const float* x_in, int n, int H, int in_ch, float* F,
+                          cudaStream_t st);
+
+// Copy finalized tiles into a dense row-major rect.
+void launch_assemble(const float* pool, const int32_t* tile_slots, int64_t ty0, int64_t tx0,
+                     int nty, int ntx, int s, int64_t y0, int64_t x0, int h, int w, float* out,
+                     int64_t pitch, cudaStream_t st);
+
+void launch_noise_fill(uint64_t seed, uint32_t level, uint32_t step, int64_t x0, int64_t y0,
+                       int w, int h, float* out, int64_t pitch, cudaStream_t st);
+
+// NCHW <-> NHWC helpers for the single-channel window images.
+void launch_nchw_to_nhwc(const float* x, int n, int c, int hw, float* y, cudaStream_t st);
+void launch_nhwc_to_nchw(const float* x, int n, int c, int hw, float* y, cudaStream_t st);
+
+// --------------------------------------------------------------- decode
+struct DecodeArgs {
+  const float* L;  int64_t lx0, ly0, lpitch; int lw, lh;
+  const float* H;  int64_t hx0, hy0, hpitch; int hw, hh;
+  int64_t x0, y0; int w, h;
+  float* out; int64_t pitch;
+  int f, R;
+  float low_mu, low_scale, res_scale;
+  const float* taps;      // device, 2R+1
+  float* D;               // scratch coarse (qh + 2R) x (qw + 2R)
+  float* T;               // scratch coarse (qh + 2R) x qw
+  float* Lhat;            // scratch coarse qh x qw
+  int64_t qx0, qy0; int qw, qh;   // coarse rect of L^ that the output reads
+};
+void launch_decode(const DecodeArgs& a, cudaStream_t st);
+
+// --------------------------------------------------------------- profiling
+// Optional per-launch CUDA-event timing on the launching stream, grouped by
+// kernel class, with the algorithmic FLOPs / bytes of each launch.
+enum ProfKind { PK_CONV_TC = 0, PK_CONV_SIMT, PK_GROUPNORM, PK_ATTENTION, PK_RESAMPLE,
+                PK_GATHER, PK_DENOISE_TEST, PK_BLEND, PK_ASSEMBLE, PK_DECODE, PK_COUNT };
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+struct Prof {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double ms[PK_COUNT] = {0}, flops[PK_COUNT] = {0}, bytes[PK_COUNT] = {0};
+  int64_t launches[PK_COUNT] = {0};
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // start a record; returns its index or -1
+  int begin(int kind, cudaStream_t st, double fl, double by) {
+    if (!on) return -1;
+    ProfRec r{kind, ev(), ev(), fl, by};
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+  }
+  void end(int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(recs[idx].b, st);
+  }
+  // fold completed records into the totals (call after a synchronize)
+  void resolve() {
+    for (auto& r : recs) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.kind] += t;
+        flops[r.kind] += r.flops;
+        bytes[r.kind] += r.bytes;
+        launches[r.kind]++;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+    cudaGetLastError();
+  }
+  void reset() {
+    for (int k = 0; k < PK_COUNT; ++k) ms[k] = flops[k] = bytes[k] = 0, launches[k] = 0;
+  }
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  }
+};
+
+// --------------------------------------------------------------- UNet
+struct UNet;  // opaque, unet.cu
+struct UNetDesc {
+  int levels;
+  std::vector<int> ch;
+  int in_ch, out_ch, groups, attn, heads, window;
+};
+// Shapes (Cout, Cin, kh, kw) in declaration order.
+std::vector<std::vector<int>> unet_param_shapes(const UNetDesc& d);
+// Create / destroy; weights are host float32 in declaration order.
+UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max_batch,
+                  Err* err);
+void unet_destroy(UNet* u);
+int unet_max_batch(const UNet* u);
+size_t unet_bytes_per_window(const UNetDesc& d, int precision);
+// x_in NHWC float32 [n][H][H][in_ch] -> F [n][H][H] float32 (out_ch = 1).
+bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err);
+int64_t unet_launches(const UNet* u);
+// device status word set by bounded device-side waits that ran out
+int* unet_status(const UNet* u);
+void unet_set_prof(UNet* u, Prof* p);
+
+// tcgen05 conv availability (compiled in conv_tc.cu)
+bool conv_tc_supported(int cin, int cout, int ks);
+
+}  // namespace idf

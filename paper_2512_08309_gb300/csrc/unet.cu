@@ -1,0 +1,624 @@
+// Window denoiser F of libidf: the synthetic ResBlock UNet (the paper's Phi,
+// Sec. 5.3, reduced to a plain conv UNet with the widths of the model stack)
+// evaluated on a batch of independent windows.
+//
+// Network (declaration order of the weights):
+//   in_conv 3x3 (in_ch -> c0);
+//   encoder level l: ResBlock(c_prev -> c_l), 2x2 average pool after every
+//     level but the last; the ResBlock output is the skip of level l;
+//   bottom: [self-attention block], ResBlock(c_{L-1} -> c_{L-1});
+//   decoder level l = L-2..0: nearest x2 upsample, concat [up, skip_l],
+//     ResBlock(c_up + c_l -> c_l);
+//   out: GroupNorm, SiLU, conv 3x3 (c0 -> out_ch).
+//   ResBlock(x) = conv2(silu(gn(conv1(silu(gn(x)))))) + (1x1 skip(x) or x).
+//   Attention: x + proj(softmax(q^T k / sqrt(d)) v), [q;k;v] = qkv(gn(x)).
+// GroupNorm uses population variance and eps = 1e-5; convolutions are zero
+// padded per window, without bias.
+//
+// Activations are NHWC (channels innermost) so that the reduction index of
+// an implicit-GEMM convolution, (tap, c_in), walks contiguous memory.  In
+// IDF_FP32 every layer runs in float32 SIMT arithmetic (the plain sampler).
+// In IDF_BF16 only the operands of the contractions are bfloat16: the
+// GroupNorm/SiLU outputs that feed a convolution and the weights; every
+// convolution output, residual and skip stays float32.  Convolutions whose
+// channel counts fit the tensor-core kernel run on tcgen05 with float32
+// accumulation (conv_tc.cu), the others in float32 SIMT arithmetic.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "internal.h"
+
+namespace idf {
+
+// ------------------------------------------------------------------ helpers
+template <typename T> __device__ __forceinline__ float ld(const T* p);
+template <> __device__ __forceinline__ float ld<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ld<bf16>(const bf16* p) { return __bfloat162float(*p); }
+template <typename T> __device__ __forceinline__ void st(T* p, float v);
+template <> __device__ __forceinline__ void st<float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void st<bf16>(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+static int grid1d(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+// ------------------------------------------------------------ SIMT conv
+// Implicit GEMM: M = n*H*W pixels, N = Cout, K = ks*ks*Cin with k = tap*Cin + ci.
+// Weights wk are float32 [K][Cout].  out = conv(x) (+ res).
+constexpr int CBM = 128, CBN = 64, CBK = 8;
+
+template <int KS, typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) conv_simt_kernel(const Tin* __restrict__ x,
+                                                        const float* __restrict__ wk,
+                                                        const Tout* __restrict__ res,
+                                                        Tout* __restrict__ y, int n, int H, int W,
+                                                        int Cin, int Cout) {
+  __shared__ float As[CBK][CBM + 4];
+  __shared__ float Bs[CBK][CBN];
+  const int tid = threadIdx.x;
+  const int64_t M = (int64_t)n * H * W;
+  const int K = KS * KS * Cin;
+  const int64_t m0 = (int64_t)blockIdx.x * CBM;
+  const int n0 = blockIdx.y * CBN;
+  const int tr = tid / 16, tc = tid % 16;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+
+  // per-thread A rows (fixed over the K loop)
+  int a_b[4], a_py[4], a_px[4];
+  bool a_ok[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + i * 256;
+    const int mm = e / CBK;
+    const int64_t m = m0 + mm;
+    a_ok[i] = m < M;
+    const int64_t mc = a_ok[i] ? m : 0;
+    a_b[i] = (int)(mc / ((int64_t)H * W));
+    const int p = (int)(mc % ((int64_t)H * W));
+    a_py[i] = p / W;
+    a_px[i] = p % W;
+  }
+  for (int k0 = 0; k0 < K; k0 += CBK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      const int kk = e % CBK, mm = e / CBK;
+      const int k = k0 + kk;
+      float v = 0.0f;
+      if (a_ok[i] && k < K) {
+        const int tap = k / Cin, ci = k - tap * Cin;
+        const int sy = a_py[i] + tap / KS - KS / 2, sx = a_px[i] + tap % KS - KS / 2;
+        if (sy >= 0 && sy < H && sx >= 0 && sx < W)
+          v = ld<Tin>(x + (((int64_t)a_b[i] * H + sy) * W + sx) * Cin + ci);
+      }
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + i * 256;
+      const int nn = e % CBN, kk = e / CBN;
+      const int k = k0 + kk, nc = n0 + nn;
+      Bs[kk][nn] = (k < K && nc < Cout) ? wk[(int64_t)k * Cout + nc] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < CBK; ++kk) {
+      float a[8], b[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[kk][tr * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tc * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + tr * 8 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nc = n0 + tc * 4 + j;
+      if (nc >= Cout) continue;
+      float v = acc[i][j];
+      if (res) v += ld<Tout>(res + m * Cout + nc);
+      st<Tout>(y + m * Cout + nc, v);
+    }
+  }
+}
+
+// ------------------------------------------------------------ GroupNorm
+// One CTA per (window, group): two-pass mean / variance with per-thread
+// float32 partial sums combined in double in a fixed tree (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) gn_stats_kernel(const T* __restrict__ x, int HW, int C,
+                                                       int G, float2* __restrict__ stats) {
+  const int b = blockIdx.x / G, g = blockIdx.x % G;
+  const int Cg = C / G;
+  const int64_t nel = (int64_t)HW * Cg;
+  const T* base = x + (int64_t)b * HW * C + g * Cg;
+  __shared__ double red[256];
+  float s = 0.0f;
+  for (int64_t e = threadIdx.x; e < nel; e += 256) {
+    const int64_t p = e / Cg;
+    const int c = (int)(e - p * Cg);
+    s += ld<T>(base + p * C + c);
+  }
+  red[threadIdx.x] = (double)s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double mean = red[0] / (double)nel;
+  __syncthreads();
+  const float mf = (float)mean;
+  float q = 0.0f;
+  for (int64_t e = threadIdx.x; e < nel; e += 256) {
+    const int64_t p = e / Cg;
+    const int c = (int)(e - p * Cg);
+    const float d = ld<T>(base + p * C + c) - mf;
+    q += d * d;
+  }
+  red[threadIdx.x] = (double)q;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double dm = mean - (double)mf;
+    const double var = red[0] / (double)nel - dm * dm;
+    stats[blockIdx.x] = make_float2((float)mean, (float)(1.0 / sqrt(var + 1e-5)));
+  }
+}
+
+// y = silu(gn(x)) (or gn(x)); when copy is given it also receives x itself
+// in the output type (the operand of a 1x1 shortcut convolution).
+template <typename Tin, typename Tout, bool SILU>
+__global__ void gn_apply_kernel(const Tin* __restrict__ x, const float2* __restrict__ stats,
+                                int64_t n_el, int HW, int C, int G, Tout* __restrict__ y,
+                                Tout* __restrict__ copy) {
+  const int Cg = C / G;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_el;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t b = i / ((int64_t)HW * C);
+    const float2 ms = stats[b * G + c / Cg];
+    const float xv = ld<Tin>(x + i);
+    float v = (xv - ms.x) * ms.y;
+    if (SILU) v = v / (1.0f + expf(-v));
+    st<Tout>(y + i, v);
+    if (copy) st<Tout>(copy + i, xv);
+  }
+}
+
+// ------------------------------------------------------------ resampling
+template <typename T>
+__global__ void avgpool2_kernel(const T* __restrict__ x, int n, int H, int W, int C,
+                                T* __restrict__ y) {
+  const int Ho = H / 2, Wo = W / 2;
+  const int64_t total = (int64_t)n * Ho * Wo * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t r = i / C;
+    const int xo = (int)(r % Wo);
+    r /= Wo;
+    const int yo = (int)(r % Ho);
+    const int64_t b = r / Ho;
+    const T* p = x + ((b * H + 2 * yo) * W + 2 * xo) * C + c;
+    const float s = (ld<T>(p) + ld<T>(p + C)) + (ld<T>(p + (int64_t)W * C) + ld<T>(p + (int64_t)W * C + C));
+    st<T>(y + i, 0.25f * s);
+  }
+}
+
+// out (n, 2h, 2w, Ca + Cb) = [nearest-up2(a), skip]
+template <typename T>
+__global__ void upcat_kernel(const T* __restrict__ a, int Ca, const T* __restrict__ sk, int Cb,
+                             int n, int H, int W, T* __restrict__ y) {
+  const int C = Ca + Cb;
+  const int64_t total = (int64_t)n * H * W * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t pix = i / C;
+    const int xx = (int)(pix % W);
+    const int64_t r = pix / W;
+    const int yy = (int)(r % H);
+    const int64_t b = r / H;
+    if (c < Ca) {
+      y[i] = a[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * Ca + c];
+    } else {
+      y[i] = sk[pix * Cb + (c - Ca)];
+    }
+  }
+}
+
+// ------------------------------------------------------------ attention
+// One CTA per (window, head); thread t owns query token t; keys and values
+// of the head are staged in shared memory as float32; online softmax.
+template <typename T>
+__global__ void attention_kernel(const float* __restrict__ qkv, int Tn, int C, int heads,
+                                 T* __restrict__ out) {
+  extern __shared__ float sm[];
+  const int d = C / heads;
+  const int b = blockIdx.x / heads, h = blockIdx.x % heads;
+  float* Ks = sm;
+  float* Vs = sm + (size_t)Tn * d;
+  const float* base = qkv + (int64_t)b * Tn * 3 * C;
+  for (int e = threadIdx.x; e < Tn * d; e += blockDim.x) {
+    const int t = e / d, c = e % d;
+    Ks[e] = base[(int64_t)t * 3 * C + C + h * d + c];
+    Vs[e] = base[(int64_t)t * 3 * C + 2 * C + h * d + c];
+  }
+  __syncthreads();
+  const float scale = rsqrtf((float)d);
+  for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
+    float q[64], o[64];
+    for (int c = 0; c < d; ++c) {
+      q[c] = base[(int64_t)t * 3 * C + h * d + c] * scale;
+      o[c] = 0.0f;
+    }
+    float mx = -INFINITY, den = 0.0f;
+    for (int j = 0; j < Tn; ++j) {
+      const float* kj = Ks + (size_t)j * d;
+      float sc = 0.0f;
+      for (int c = 0; c < d; ++c) sc = fmaf(q[c], kj[c], sc);
+      if (sc > mx) {
+        const float corr = expf(mx - sc);
+        den *= corr;
+        for (int c = 0; c < d; ++c) o[c] *= corr;
+        mx = sc;
+      }
+      const float pj = expf(sc - mx);
+      den += pj;
+      const float* vj = Vs + (size_t)j * d;
+      for (int c = 0; c < d; ++c) o[c] = fmaf(pj, vj[c], o[c]);
+    }
+    const float inv = 1.0f / den;
+    for (int c = 0; c < d; ++c) st<T>(out + ((int64_t)b * Tn + t) * C + h * d + c, o[c] * inv);
+  }
+}
+
+// ------------------------------------------------------------ engine
+bool conv_tc_forward(const bf16* x, const bf16* w, const float* res, float* y, int n, int H, int W,
+                     int Cin, int Cout, int ks, int* status, cudaStream_t st, std::string* err);
+bool conv_tc_shape_ok(int H, int W);
+
+struct ConvW {
+  int cin = 0, cout = 0, ks = 0;
+  float* w32 = nullptr;  // [K][Cout], k = tap*Cin + ci
+  bf16* w16 = nullptr;   // [tap][Cout][Cin] (tensor-core layout) or null
+  bool tc = false;
+};
+
+// Per resolution level: float32 buffers P (encoder input), SK (skip), CAT
+// (decoder concat), M (block output), T2, T3 (conv outputs) and operand
+// buffers T1, T4 (GroupNorm/SiLU output, shortcut operand) in the operand type.
+struct LevelBufs {
+  int H = 0;
+  size_t cmax = 0;
+  void* P = nullptr;
+  void* SK = nullptr;
+  void* CAT = nullptr;
+  void* M = nullptr;
+  void* T1 = nullptr;
+  void* T2 = nullptr;
+  void* T3 = nullptr;
+  void* T4 = nullptr;
+};
+
+struct UNet {
+  UNetDesc d;
+  int precision = 0;
+  int max_batch = 0;
+  std::vector<ConvW> convs;
+  std::vector<LevelBufs> lv;
+  float2* stats = nullptr;
+  int* status = nullptr;
+  int64_t launches = 0;
+  Prof* prof = nullptr;
+};
+
+std::vector<std::vector<int>> unet_param_shapes(const UNetDesc& d) {
+  std::vector<std::vector<int>> s;
+  const int L = d.levels;
+  s.push_back({d.ch[0], d.in_ch, 3, 3});
+  auto rb = [&](int cin, int cout) {
+    s.push_back({cout, cin, 3, 3});
+    s.push_back({cout, cout, 3, 3});
+    if (cin != cout) s.push_back({cout, cin, 1, 1});
+  };
+  int prev = d.ch[0];
+  for (int l = 0; l < L; ++l) {
+    rb(prev, d.ch[l]);
+    prev = d.ch[l];
+  }
+  if (d.attn) {
+    s.push_back({3 * prev, prev, 1, 1});
+    s.push_back({prev, prev, 1, 1});
+  }
+  rb(prev, prev);
+  for (int l = L - 2; l >= 0; --l) {
+    rb(prev + d.ch[l], d.ch[l]);
+    prev = d.ch[l];
+  }
+  s.push_back({d.out_ch, prev, 3, 3});
+  return s;
+}
+
+// Largest channel count any buffer of resolution level l holds.
+static size_t level_cmax(const UNetDesc& d, int l) {
+  size_t c = (size_t)std::max(d.ch[l], l > 0 ? d.ch[l - 1] : d.ch[0]);
+  if (l + 1 < d.levels) c = std::max(c, (size_t)(d.ch[l] + d.ch[l + 1]));  // decoder concat
+  if (l == d.levels - 1 && d.attn) c = std::max(c, (size_t)3 * d.ch[l]);   // qkv
+  return c;
+}
+
+size_t unet_bytes_per_window(const UNetDesc& d, int precision) {
+  (void)precision;
+  size_t t = 0;
+  for (int l = 0; l < d.levels; ++l) {
+    const size_t H = (size_t)(d.window >> l);
+    t += 8 * H * H * level_cmax(d, l) * 4;
+  }
+  return t;
+}
+
+static bool ck(cudaError_t e, Err* err, const char* what) {
+  if (e == cudaSuccess) return true;
+  if (err) {
+    err->code = e == cudaErrorMemoryAllocation ? 2 : 3;
+    err->msg = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  cudaGetLastError();
+  return false;
+}
+
+void unet_destroy(UNet* u) {
+  if (!u) return;
+  for (auto& c : u->convs) {
+    cudaFree(c.w32);
+    cudaFree(c.w16);
+  }
+  for (auto& b : u->lv) {
+    cudaFree(b.P); cudaFree(b.SK); cudaFree(b.CAT); cudaFree(b.M);
+    cudaFree(b.T1); cudaFree(b.T2); cudaFree(b.T3); cudaFree(b.T4);
+  }
+  cudaFree(u->stats);
+  cudaFree(u->status);
+  delete u;
+}
+
+UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max_batch, Err* err) {
+  UNet* u = new UNet();
+  u->d = d;
+  u->precision = precision;
+  u->max_batch = std::max(1, max_batch);
+  auto shapes = unet_param_shapes(d);
+  size_t off = 0;
+  // resolution of each conv, to know whether the tensor-core kernel applies
+  for (auto& s : shapes) {
+    ConvW c;
+    c.cout = s[0];
+    c.cin = s[1];
+    c.ks = s[2];
+    const int taps = c.ks * c.ks;
+    const size_t K = (size_t)taps * c.cin;
+    std::vector<float> pk(K * c.cout);
+    // (Cout, Cin, kh, kw) -> [tap*Cin + ci][Cout]
+    for (int o = 0; o < c.cout; ++o)
+      for (int ci = 0; ci < c.cin; ++ci)
+        for (int t = 0; t < taps; ++t)
+          pk[((size_t)t * c.cin + ci) * c.cout + o] = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
+    if (!ck(cudaMalloc(&c.w32, pk.size() * 4), err, "cudaMalloc weights")) { unet_destroy(u); return nullptr; }
+    if (!ck(cudaMemcpy(c.w32, pk.data(), pk.size() * 4, cudaMemcpyHostToDevice), err, "copy weights")) { unet_destroy(u); return nullptr; }
+    if (precision == 1 && conv_tc_supported(c.cin, c.cout, c.ks)) {
+      // (Cout, Cin, kh, kw) -> [tap][Cout][Cin] bfloat16
+      std::vector<bf16> p16((size_t)taps * c.cout * c.cin);
+      for (int o = 0; o < c.cout; ++o)
+        for (int ci = 0; ci < c.cin; ++ci)
+          for (int t = 0; t < taps; ++t)
+            p16[((size_t)t * c.cout + o) * c.cin + ci] =
+                __float2bfloat16_rn(w_host[off + ((size_t)o * c.cin + ci) * taps + t]);
+      if (!ck(cudaMalloc(&c.w16, p16.size() * 2), err, "cudaMalloc bf16 weights")) { unet_destroy(u); return nullptr; }
+      if (!ck(cudaMemcpy(c.w16, p16.data(), p16.size() * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")) { unet_destroy(u); return nullptr; }
+      c.tc = true;
+    }
+    off += (size_t)c.cout * c.cin * taps;
+    u->convs.push_back(c);
+  }
+  const size_t B = (size_t)u->max_batch;
+  for (int l = 0; l < d.levels; ++l) {
+    LevelBufs b;
+    b.H = d.window >> l;
+    b.cmax = level_cmax(d, l);
+    const size_t bytes = B * b.H * b.H * b.cmax * 4;
+    void** ps[8] = {&b.P, &b.SK, &b.CAT, &b.M, &b.T1, &b.T2, &b.T3, &b.T4};
+    bool ok = true;
+    for (auto p : ps)
+      if (ok && !ck(cudaMalloc(p, bytes), err, "cudaMalloc UNet workspace")) ok = false;
+    u->lv.push_back(b);
+    if (!ok) { unet_destroy(u); return nullptr; }
+  }
+  if (!ck(cudaMalloc(&u->stats, B * d.groups * sizeof(float2)), err, "cudaMalloc stats")) { unet_destroy(u); return nullptr; }
+  if (!ck(cudaMalloc(&u->status, sizeof(int)), err, "cudaMalloc status") ||
+      !ck(cudaMemset(u->status, 0, sizeof(int)), err, "memset status")) { unet_destroy(u); return nullptr; }
+  return u;
+}
+
+int unet_max_batch(const UNet* u) { return u->max_batch; }
+int64_t unet_launches(const UNet* u) { return u->launches; }
+int* unet_status(const UNet* u) { return u->status; }
+void unet_set_prof(UNet* u, Prof* p) { u->prof = p; }
+
+namespace {
+
+struct Ctx {
+  UNet* u;
+  int n;
+  cudaStream_t st;
+  Err* err;
+  bool ok = true;
+};
+
+// out (float32) = conv(x) (+ res), x in operand type TA (or float32 x_f32)
+template <typename TA>
+void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H) {
+  if (!c.ok) return;
+  const int W = H;
+  const double flops = 2.0 * c.n * H * W * (double)w.cout * w.ks * w.ks * w.cin;
+  if (std::is_same<TA, bf16>::value && w.tc && !x_f32 && conv_tc_shape_ok(H, W)) {
+    std::string e;
+    // algorithmic bytes: bf16 operand read once, weights, float32 output (+ residual)
+    const double by = c.n * H * W * (2.0 * w.cin + 4.0 * w.cout * (res ? 2 : 1)) + 2.0 * w.ks * w.ks * w.cin * w.cout;
+    const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
+    const bool ok = conv_tc_forward((const bf16*)x, w.w16, res, y, c.n, H, W, w.cin, w.cout, w.ks,
+                         c.u->status, c.st, &e);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    if (!ok) {
+      c.ok = false;
+      c.err->code = 3;
+      c.err->msg = "conv_tc: " + e;
+    }
+    c.u->launches++;
+    return;
+  }
+  const int64_t M = (int64_t)c.n * H * W;
+  dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((w.cout + CBN - 1) / CBN));
+  const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, flops, 0.0) : -1;
+  if (w.ks == 3) {
+    if (x_f32) conv_simt_kernel<3, float, float><<<grid, 256, 0, c.st>>>((const float*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
+    else conv_simt_kernel<3, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
+  } else {
+    if (x_f32) conv_simt_kernel<1, float, float><<<grid, 256, 0, c.st>>>((const float*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
+    else conv_simt_kernel<1, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
+  }
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+  c.u->launches++;
+}
+
+// y (TA) = silu(gn(x)) or gn(x); copy (TA, optional) = x
+template <typename TA>
+void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = nullptr) {
+  if (!c.ok) return;
+  const int G = c.u->d.groups;
+  const double nb = (double)c.n * H * H * C;
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (8.0 + 4.0 + sizeof(TA) * (copy ? 2 : 1))) : -1;
+  gn_stats_kernel<float><<<c.n * G, 256, 0, c.st>>>(x, H * H, C, G, c.u->stats);
+  const int64_t nel = (int64_t)c.n * H * H * C;
+  if (silu)
+    gn_apply_kernel<float, TA, true><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy);
+  else
+    gn_apply_kernel<float, TA, false><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy);
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+  c.u->launches += 2;
+}
+
+// ResBlock: X (cin, float32) -> Y (cout, float32).
+template <typename TA>
+void resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, int cout, float* Y) {
+  const ConvW& c1 = c.u->convs[wi++];
+  const ConvW& c2 = c.u->convs[wi++];
+  const ConvW* sk = nullptr;
+  if (cin != cout) sk = &c.u->convs[wi++];
+  const bool need_copy = sk && !std::is_same<TA, float>::value;
+  gn<TA>(c, X, b.H, cin, b.T1, true, need_copy ? b.T4 : nullptr);
+  conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H);
+  const float* res = X;
+  if (sk) {
+    if (need_copy) conv_run<TA>(c, *sk, b.T4, false, nullptr, (float*)b.T3, b.H);
+    else conv_run<TA>(c, *sk, X, true, nullptr, (float*)b.T3, b.H);
+    res = (const float*)b.T3;
+  }
+  gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true);
+  conv_run<TA>(c, c2, b.T1, false, res, Y, b.H);
+}
+
+template <typename TA>
+bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err) {
+  Ctx c{u, n, st, err};
+  const UNetDesc& d = u->d;
+  const int L = d.levels;
+  size_t wi = 0;
+  conv_run<TA>(c, u->convs[wi++], x_in, true, nullptr, (float*)u->lv[0].P, d.window);
+  int prev = d.ch[0];
+  for (int l = 0; l < L; ++l) {
+    LevelBufs& b = u->lv[l];
+    resblock<TA>(c, wi, b, (const float*)b.P, prev, d.ch[l], (float*)b.SK);
+    prev = d.ch[l];
+    if (l < L - 1) {
+      const int64_t tot = (int64_t)n * (b.H / 2) * (b.H / 2) * prev;
+      avgpool2_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>((const float*)b.SK, n, b.H, b.H, prev, (float*)u->lv[l + 1].P);
+      u->launches++;
+    }
+  }
+  LevelBufs& bl = u->lv[L - 1];
+  const float* cur = (const float*)bl.SK;
+  if (d.attn) {
+    const ConvW& qkv = u->convs[wi++];
+    const ConvW& proj = u->convs[wi++];
+    gn<TA>(c, cur, bl.H, prev, bl.T1, false);
+    conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H);
+    const int Tn = bl.H * bl.H, dh = prev / d.heads;
+    const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
+    cudaFuncSetAttribute(attention_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int pr = u->prof ? u->prof->begin(PK_ATTENTION, st, 4.0 * n * (double)Tn * Tn * prev, 0.0) : -1;
+    attention_kernel<TA><<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3);
+    if (u->prof) u->prof->end(pr, st);
+    u->launches++;
+    conv_run<TA>(c, proj, bl.T3, false, cur, (float*)bl.CAT, bl.H);
+    cur = (const float*)bl.CAT;
+  }
+  resblock<TA>(c, wi, bl, cur, prev, prev, (float*)bl.M);
+  for (int l = L - 2; l >= 0; --l) {
+    LevelBufs& b = u->lv[l];
+    const int64_t tot = (int64_t)n * b.H * b.H * (prev + d.ch[l]);
+    upcat_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>((const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], n, b.H, b.H, (float*)b.CAT);
+    u->launches++;
+    resblock<TA>(c, wi, b, (const float*)b.CAT, prev + d.ch[l], d.ch[l], (float*)b.M);
+    prev = d.ch[l];
+  }
+  LevelBufs& b0 = u->lv[0];
+  gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true);
+  conv_run<TA>(c, u->convs[wi++], b0.T1, false, nullptr, F, d.window);
+  if (c.ok) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      err->code = 3;
+      err->msg = std::string("UNet launch: ") + cudaGetErrorString(e);
+      return false;
+    }
+  }
+  return c.ok;
+}
+
+}  // namespace
+
+bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err) {
+  if (n > u->max_batch) {
+    err->code = 7;
+    err->msg = "UNet batch larger than its workspace";
+    return false;
+  }
+  if (n <= 0) return true;
+  if (u->precision == 1) return forward_t<bf16>(u, x_in, n, F, st, err);
+  return forward_t<float>(u, x_in, n, F, st, err);
+}
+
+}  // namespace idf
