@@ -207,6 +207,281 @@ __global__ void gn_apply_kernel(const Tin* __restrict__ x, const float2* __restr
   }
 }
 
+// Fast GroupNorm for channel counts with (C / G) % 8 == 0.
+// Pass 1 (gn_partial): CTA (chunk, group, window) streams the group's
+// channels of a contiguous run of pixels; every value is shifted by the
+// group's first value in the window (a sample of the same distribution, so
+// the variance formula below does not cancel), and the shifted sum and sum
+// of squares are reduced in a fixed tree (warp shuffles, then warps in
+// order) into one partial per (window, group, chunk) in a scratch array.
+// Pass 2 (gn_finalize): one thread per (window, group) adds the chunks in
+// order in double and forms mean and 1/sqrt(var + eps).  Nothing depends on
+// how windows are batched.
+__global__ void __launch_bounds__(256) gn_partial_kernel(const float* __restrict__ x, int HW, int C,
+                                                         int G, int chunk_px,
+                                                         double2* __restrict__ part) {
+  __shared__ float r1[8], r2[8];
+  const int Cg = C / G;
+  const int Q = Cg / 4;            // float4 per pixel of the group
+  const int P = blockDim.x / Q;    // pixels in flight
+  const int t = threadIdx.x;
+  const int q = t % Q, pl = t / Q;
+  const int chunk = blockIdx.x, g = blockIdx.y, b = blockIdx.z;
+  const int p0 = chunk * chunk_px;
+  const int p1 = min(HW, p0 + chunk_px);
+  const float* wb = x + (int64_t)b * HW * C + g * Cg;
+  const float k = wb[0];
+  float s1 = 0.0f, s2 = 0.0f;
+  if (pl < P) {
+    for (int p = p0 + pl; p < p1; p += P) {
+      const float4 v = *reinterpret_cast<const float4*>(wb + (int64_t)p * C + 4 * q);
+      const float a = v.x - k, bb = v.y - k, c = v.z - k, d = v.w - k;
+      s1 += (a + bb) + (c + d);
+      s2 += (a * a + bb * bb) + (c * c + d * d);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if ((t & 31) == 0) {
+    r1[t >> 5] = s1;
+    r2[t >> 5] = s2;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += (double)r1[w];
+      c += (double)r2[w];
+    }
+    part[((int64_t)b * G + g) * gridDim.x + chunk] = make_double2(a, c);
+  }
+}
+
+__global__ void gn_finalize_kernel(const float* __restrict__ x, const double2* __restrict__ part,
+                                   int n_win, int chunks, int HW, int C, int G,
+                                   float2* __restrict__ stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_win * G) return;
+  const int b = i / G, g = i % G;
+  const int Cg = C / G;
+  double s1 = 0.0, s2 = 0.0;
+  for (int c = 0; c < chunks; ++c) {
+    const double2 pp = part[(int64_t)i * chunks + c];
+    s1 += pp.x;
+    s2 += pp.y;
+  }
+  const double n = (double)HW * Cg;
+  const double k = (double)x[(int64_t)b * HW * C + g * Cg];
+  const double m1 = s1 / n;
+  const double var = fmax(0.0, s2 / n - m1 * m1);
+  stats[i] = make_float2((float)(k + m1), (float)(1.0 / sqrt(var + 1e-5)));
+}
+
+// y = silu(gn(x)) (or gn(x)) on 8 channels (one group) per thread; copy = x.
+template <typename TA> struct Pack8;
+template <> struct Pack8<float> {
+  static __device__ __forceinline__ void store(float* p, const float (&v)[8]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <> struct Pack8<bf16> {
+  static __device__ __forceinline__ void store(bf16* p, const float (&v)[8]) {
+    uint4 u;
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]);
+    __nv_bfloat162 h3 = __floats2bfloat162_rn(v[6], v[7]);
+    u.x = *reinterpret_cast<uint32_t*>(&h0);
+    u.y = *reinterpret_cast<uint32_t*>(&h1);
+    u.z = *reinterpret_cast<uint32_t*>(&h2);
+    u.w = *reinterpret_cast<uint32_t*>(&h3);
+    *reinterpret_cast<uint4*>(p) = u;
+  }
+};
+
+template <typename TA, bool SILU>
+__global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict__ x,
+                                                        const float2* __restrict__ stats,
+                                                        int n_units, int units_per_win, int C,
+                                                        int G, TA* __restrict__ y,
+                                                        TA* __restrict__ copy) {
+  const int C8 = C / 8, Cg = C / G;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+    const int b = u / units_per_win;
+    const int c0 = (u % C8) * 8;
+    const float2 ms = stats[b * G + c0 / Cg];
+    const float4* src = reinterpret_cast<const float4*>(x + (int64_t)u * 8);
+    const float4 a = src[0], bq = src[1];
+    float xv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float z = (xv[j] - ms.x) * ms.y;
+      if (SILU) z = z / (1.0f + expf(-z));
+      v[j] = z;
+    }
+    Pack8<TA>::store(y + (int64_t)u * 8, v);
+    if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+  }
+}
+
+// ------------------------------------------------------------ thin convolutions
+// In-conv (C_in <= 4 -> C_out): thread per (pixel, 4 output channels).
+template <int CIN>
+__global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ x,
+                                                      const float* __restrict__ wk,
+                                                      float* __restrict__ y, int n, int H, int W,
+                                                      int Cout) {
+  const int Q = Cout / 4;
+  const int64_t total = (int64_t)n * H * W * Q;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i % Q);
+    const int64_t m = i / Q;
+    const int px = (int)(m % W);
+    const int64_t r = m / W;
+    const int py = (int)(r % H);
+    const int64_t b = r / H;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int sy = py + tap / 3 - 1, sx = px + tap % 3 - 1;
+      if (sy < 0 || sy >= H || sx < 0 || sx >= W) continue;
+      const float* xp = x + ((b * H + sy) * W + sx) * CIN;
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) {
+        const float xv = xp[ci];
+        const float4 w4 = __ldg(reinterpret_cast<const float4*>(wk + (int64_t)(tap * CIN + ci) * Cout) + q);
+        acc.x = fmaf(xv, w4.x, acc.x);
+        acc.y = fmaf(xv, w4.y, acc.y);
+        acc.z = fmaf(xv, w4.z, acc.z);
+        acc.w = fmaf(xv, w4.w, acc.w);
+      }
+    }
+    reinterpret_cast<float4*>(y + m * Cout)[q] = acc;
+  }
+}
+
+// Out-conv (C_in -> 1): thread per output pixel, 8 input channels per load.
+template <typename T> struct Load8;
+template <> struct Load8<float> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+template <> struct Load8<bf16> {
+  static __device__ __forceinline__ void load(const bf16* p, float (&v)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(h[j]);
+      v[2 * j] = f.x;
+      v[2 * j + 1] = f.y;
+    }
+  }
+};
+
+template <typename TA>
+__global__ void __launch_bounds__(256) conv_out_kernel(const TA* __restrict__ x,
+                                                       const float* __restrict__ wk,
+                                                       float* __restrict__ y, int n, int H, int W,
+                                                       int Cin) {
+  extern __shared__ float wsm[];  // [9][Cin]
+  for (int i = threadIdx.x; i < 9 * Cin; i += blockDim.x) wsm[i] = wk[i];
+  __syncthreads();
+  const int64_t total = (int64_t)n * H * W;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < total;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const int px = (int)(m % W);
+    const int64_t r = m / W;
+    const int py = (int)(r % H);
+    const int64_t b = r / H;
+    float acc = 0.0f;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int sy = py + tap / 3 - 1, sx = px + tap % 3 - 1;
+      if (sy < 0 || sy >= H || sx < 0 || sx >= W) continue;
+      const TA* xp = x + ((b * H + sy) * W + sx) * Cin;
+      const float* wp = wsm + tap * Cin;
+      for (int c = 0; c < Cin; c += 8) {
+        float v[8];
+        Load8<TA>::load(xp + c, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc = fmaf(v[j], wp[c + j], acc);
+      }
+    }
+    y[m] = acc;
+  }
+}
+
+// Attention with a compile-time head width: query and output rows stay in
+// registers; keys and values of the head are staged in shared memory.
+template <typename T, int D>
+__global__ void attention_d_kernel(const float* __restrict__ qkv, int Tn, int C, int heads,
+                                   T* __restrict__ out) {
+  extern __shared__ float sm[];
+  const int b = blockIdx.x / heads, h = blockIdx.x % heads;
+  float* Ks = sm;
+  float* Vs = sm + (size_t)Tn * D;
+  const float* base = qkv + (int64_t)b * Tn * 3 * C;
+  for (int e = threadIdx.x; e < Tn * D / 4; e += blockDim.x) {
+    const int t = (4 * e) / D, c = (4 * e) % D;
+    reinterpret_cast<float4*>(Ks)[e] = *reinterpret_cast<const float4*>(base + (int64_t)t * 3 * C + C + h * D + c);
+    reinterpret_cast<float4*>(Vs)[e] = *reinterpret_cast<const float4*>(base + (int64_t)t * 3 * C + 2 * C + h * D + c);
+  }
+  __syncthreads();
+  const float scale = rsqrtf((float)D);
+  for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
+    float q[D], o[D];
+    const float* qp = base + (int64_t)t * 3 * C + h * D;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      q[c] = qp[c] * scale;
+      o[c] = 0.0f;
+    }
+    float mx = -INFINITY, den = 0.0f;
+    for (int j = 0; j < Tn; ++j) {
+      const float4* kj = reinterpret_cast<const float4*>(Ks + (size_t)j * D);
+      float sc = 0.0f;
+#pragma unroll
+      for (int c = 0; c < D / 4; ++c) {
+        const float4 k4 = kj[c];
+        sc = fmaf(q[4 * c], k4.x, sc);
+        sc = fmaf(q[4 * c + 1], k4.y, sc);
+        sc = fmaf(q[4 * c + 2], k4.z, sc);
+        sc = fmaf(q[4 * c + 3], k4.w, sc);
+      }
+      if (sc > mx) {
+        const float corr = expf(mx - sc);
+        den *= corr;
+#pragma unroll
+        for (int c = 0; c < D; ++c) o[c] *= corr;
+        mx = sc;
+      }
+      const float pj = expf(sc - mx);
+      den += pj;
+      const float4* vj = reinterpret_cast<const float4*>(Vs + (size_t)j * D);
+#pragma unroll
+      for (int c = 0; c < D / 4; ++c) {
+        const float4 v4 = vj[c];
+        o[4 * c] = fmaf(pj, v4.x, o[4 * c]);
+        o[4 * c + 1] = fmaf(pj, v4.y, o[4 * c + 1]);
+        o[4 * c + 2] = fmaf(pj, v4.z, o[4 * c + 2]);
+        o[4 * c + 3] = fmaf(pj, v4.w, o[4 * c + 3]);
+      }
+    }
+    const float inv = 1.0f / den;
+    T* op = out + ((int64_t)b * Tn + t) * C + h * D;
+#pragma unroll
+    for (int c = 0; c < D; ++c) st<T>(op + c, o[c] * inv);
+  }
+}
+
 // ------------------------------------------------------------ resampling
 template <typename T>
 __global__ void avgpool2_kernel(const T* __restrict__ x, int n, int H, int W, int C,
@@ -330,10 +605,13 @@ struct UNet {
   std::vector<ConvW> convs;
   std::vector<LevelBufs> lv;
   float2* stats = nullptr;
+  double2* gnpart = nullptr;  // GroupNorm partials (scratch), max_batch * groups * GN_MAX_CHUNKS
   int* status = nullptr;
   int64_t launches = 0;
   Prof* prof = nullptr;
 };
+
+constexpr int GN_MAX_CHUNKS = 1024;
 
 std::vector<std::vector<int>> unet_param_shapes(const UNetDesc& d) {
   std::vector<std::vector<int>> s;
@@ -370,14 +648,15 @@ static size_t level_cmax(const UNetDesc& d, int l) {
   return c;
 }
 
+// six float32 buffers and two operand buffers per resolution level
 size_t unet_bytes_per_window(const UNetDesc& d, int precision) {
-  (void)precision;
+  const size_t ea = precision == 1 ? 2 : 4;
   size_t t = 0;
   for (int l = 0; l < d.levels; ++l) {
     const size_t H = (size_t)(d.window >> l);
-    t += 8 * H * H * level_cmax(d, l) * 4;
+    t += (6 * 4 + 2 * ea) * H * H * level_cmax(d, l);
   }
-  return t;
+  return t + (size_t)GN_MAX_CHUNKS * d.groups * sizeof(double2);
 }
 
 static bool ck(cudaError_t e, Err* err, const char* what) {
@@ -401,6 +680,7 @@ void unet_destroy(UNet* u) {
     cudaFree(b.T1); cudaFree(b.T2); cudaFree(b.T3); cudaFree(b.T4);
   }
   cudaFree(u->stats);
+  cudaFree(u->gnpart);
   cudaFree(u->status);
   delete u;
 }
@@ -449,14 +729,16 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
     b.H = d.window >> l;
     b.cmax = level_cmax(d, l);
     const size_t bytes = B * b.H * b.H * b.cmax * 4;
-    void** ps[8] = {&b.P, &b.SK, &b.CAT, &b.M, &b.T1, &b.T2, &b.T3, &b.T4};
+    const size_t obytes = B * b.H * b.H * b.cmax * (precision == 1 ? 2 : 4);
+    void** ps[8] = {&b.P, &b.SK, &b.CAT, &b.M, &b.T2, &b.T3, &b.T1, &b.T4};
     bool ok = true;
-    for (auto p : ps)
-      if (ok && !ck(cudaMalloc(p, bytes), err, "cudaMalloc UNet workspace")) ok = false;
+    for (int i = 0; i < 8; ++i)
+      if (ok && !ck(cudaMalloc(ps[i], i < 6 ? bytes : obytes), err, "cudaMalloc UNet workspace")) ok = false;
     u->lv.push_back(b);
     if (!ok) { unet_destroy(u); return nullptr; }
   }
   if (!ck(cudaMalloc(&u->stats, B * d.groups * sizeof(float2)), err, "cudaMalloc stats")) { unet_destroy(u); return nullptr; }
+  if (!ck(cudaMalloc(&u->gnpart, B * GN_MAX_CHUNKS * d.groups * sizeof(double2)), err, "cudaMalloc GroupNorm scratch")) { unet_destroy(u); return nullptr; }
   if (!ck(cudaMalloc(&u->status, sizeof(int)), err, "cudaMalloc status") ||
       !ck(cudaMemset(u->status, 0, sizeof(int)), err, "memset status")) { unet_destroy(u); return nullptr; }
   return u;
@@ -500,8 +782,22 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     return;
   }
   const int64_t M = (int64_t)c.n * H * W;
-  dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((w.cout + CBN - 1) / CBN));
   const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, flops, 0.0) : -1;
+  if (w.ks == 3 && x_f32 && !res && w.cin <= 2 && w.cout % 4 == 0) {
+    const int64_t tot = M * (w.cout / 4);
+    if (w.cin == 1) conv_in_kernel<1><<<grid1d(tot, 256), 256, 0, c.st>>>((const float*)x, w.w32, y, c.n, H, W, w.cout);
+    else conv_in_kernel<2><<<grid1d(tot, 256), 256, 0, c.st>>>((const float*)x, w.w32, y, c.n, H, W, w.cout);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches++;
+    return;
+  }
+  if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 8 == 0) {
+    conv_out_kernel<TA><<<grid1d(M, 256), 256, 9 * w.cin * sizeof(float), c.st>>>((const TA*)x, w.w32, y, c.n, H, W, w.cin);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches++;
+    return;
+  }
+  dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((w.cout + CBN - 1) / CBN));
   if (w.ks == 3) {
     if (x_f32) conv_simt_kernel<3, float, float><<<grid, 256, 0, c.st>>>((const float*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
     else conv_simt_kernel<3, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
@@ -519,7 +815,32 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
   if (!c.ok) return;
   const int G = c.u->d.groups;
   const double nb = (double)c.n * H * H * C;
-  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (8.0 + 4.0 + sizeof(TA) * (copy ? 2 : 1))) : -1;
+  // algorithmic bytes: statistics pass and apply pass each read the float32
+  // input once; the apply pass writes the operand (and the copy)
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (8.0 + sizeof(TA) * (copy ? 2 : 1))) : -1;
+  const int HW = H * H;
+  const int Cg = C / G;
+  const int64_t units = (int64_t)c.n * HW * (C / 8);
+  if (C % 8 == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31)) {
+    // each CTA reduces about 8192 values of one group
+    const int Q = Cg / 4, P = 256 / Q;
+    int chunk_px = std::max(P, 8192 / Cg);
+    int chunks = (HW + chunk_px - 1) / chunk_px;
+    if (chunks > GN_MAX_CHUNKS) {
+      chunk_px = (HW + GN_MAX_CHUNKS - 1) / GN_MAX_CHUNKS;
+      chunks = (HW + chunk_px - 1) / chunk_px;
+    }
+    gn_partial_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(x, HW, C, G, chunk_px, c.u->gnpart);
+    gn_finalize_kernel<<<(c.n * G + 127) / 128, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
+    const int upw = HW * (C / 8);
+    if (silu)
+      gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy);
+    else
+      gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches += 3;
+    return;
+  }
   gn_stats_kernel<float><<<c.n * G, 256, 0, c.st>>>(x, H * H, C, G, c.u->stats);
   const int64_t nel = (int64_t)c.n * H * H * C;
   if (silu)
@@ -577,9 +898,15 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H);
     const int Tn = bl.H * bl.H, dh = prev / d.heads;
     const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
-    cudaFuncSetAttribute(attention_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int pr = u->prof ? u->prof->begin(PK_ATTENTION, st, 4.0 * n * (double)Tn * Tn * prev, 0.0) : -1;
-    attention_kernel<TA><<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3);
+    if (dh == 64 || dh == 32 || dh == 16) {
+      auto kern = dh == 64 ? attention_d_kernel<TA, 64> : dh == 32 ? attention_d_kernel<TA, 32> : attention_d_kernel<TA, 16>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3);
+    } else {
+      cudaFuncSetAttribute(attention_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attention_kernel<TA><<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3);
+    }
     if (u->prof) u->prof->end(pr, st);
     u->launches++;
     conv_run<TA>(c, proj, bl.T3, false, cur, (float*)bl.CAT, bl.H);

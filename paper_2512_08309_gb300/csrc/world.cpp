@@ -814,7 +814,7 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
   if (cudaMalloc(&W->d_err, sizeof(int)) != cudaSuccess || cudaMemset(W->d_err, 0, sizeof(int)) != cudaSuccess)
     return bail(IDF_ECUDA);
   const size_t cache_bytes = opts->cache_bytes ? opts->cache_bytes : ((size_t)8 << 30);
-  const size_t ws_bytes = opts->workspace_bytes ? opts->workspace_bytes : ((size_t)16 << 30);
+  const size_t ws_bytes = opts->workspace_bytes ? opts->workspace_bytes : ((size_t)48 << 30);
   W->prof.on = opts->profile != 0;
   W->lv.resize(stack->n_levels);
   for (int i = 0; i < stack->n_levels; ++i) {
