@@ -221,6 +221,27 @@ idf_status idf_laplacian_decode(const idf_model_stack* stack, const float* L_dev
                                 int32_t h, float* out_dev, int64_t pitch_elems,
                                 void* cuda_stream);
 
+/* The same decode as idf_laplacian_decode, for callers that cannot allocate
+ * device memory at call time (a plugin whose host engine owns all device
+ * memory through its own pool, a frame loop that cannot take an allocation's
+ * latency or implicit synchronization).  The paper has no counterpart; this
+ * is a deployment variant.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine: its scratch (2^20 floats, 4 MiB) is a fixed array in the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits.  Queries whose scratch would exceed it (anything larger
+ * than about 4096 x 4096 pixels at lap_factor 8, lap_radius 15) return
+ * IDF_EINVAL.  Runs on the current device; the first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture.  All calls on a device share the array: calls
+ * whose kernels overlap on the GPU race and must be ordered by the caller.
+ * Arguments and results are those of idf_laplacian_decode. */
+idf_status idf_laplacian_decode_noalloc(const idf_model_stack* stack, const float* L_dev, int64_t lx0,
+                                        int64_t ly0, int32_t lw, int32_t lh, int64_t lpitch,
+                                        const float* H_dev, int64_t hx0, int64_t hy0, int32_t hw,
+                                        int32_t hh, int64_t hpitch, int64_t x0, int64_t y0, int32_t w,
+                                        int32_t h, float* out_dev, int64_t pitch_elems,
+                                        void* cuda_stream);
+
 /* Halo the decode of [x0, x0+w) x [y0, y0+h) reads: the coarse rect of L and
  * the fine rect of H, each as (x0, y0, w, h). */
 idf_status idf_laplacian_halo(const idf_model_stack* stack, int64_t x0, int64_t y0, int32_t w,

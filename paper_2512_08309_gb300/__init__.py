@@ -29,7 +29,7 @@ EXPORTS = [
     "idf_world_create", "idf_world_query", "idf_world_query_device", "idf_world_query_batch",
     "idf_world_cache_clear", "idf_world_stats", "idf_world_last_error", "idf_world_destroy",
     "idf_debug_cone", "idf_noise_fill", "idf_model_param_count", "idf_model_param_shape",
-    "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo",
+    "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo", "idf_laplacian_decode_noalloc",
 ]
 
 
@@ -105,6 +105,8 @@ def lib():
                                   i32, i32, i64, i64, i64, i32, i32, vp, i64, vp], i32),
         "idf_laplacian_halo": ([C.POINTER(idf_model_stack), i64, i64, i32, i32, C.POINTER(i64),
                                 C.POINTER(i64)], i32),
+        "idf_laplacian_decode_noalloc": ([C.POINTER(idf_model_stack), vp, i64, i64, i32, i32, i64, vp, i64,
+                                          i64, i32, i32, i64, i64, i64, i32, i32, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -300,3 +302,16 @@ def laplacian_decode(stack: dict, L_ptr: int, lrect, lpitch: int, H_ptr: int, hr
                                       lpitch, C.c_void_p(H_ptr), hrect[0], hrect[1], hrect[2], hrect[3], hpitch,
                                       x0, y0, w, h, C.c_void_p(out_ptr), pitch, _stream_ptr(stream)),
            "idf_laplacian_decode")
+
+
+def laplacian_decode_noalloc(stack: dict, L_ptr: int, lrect, lpitch: int, H_ptr: int, hrect, hpitch: int,
+                             x0: int, y0: int, w: int, h: int, out_ptr: int, pitch: int, stream=None):
+    """idf_laplacian_decode_noalloc: the decode without device allocation
+    (fixed 4 MiB scratch in the library; see include/idf.h)."""
+    keep = _Keep()
+    st = model_stack(stack, None, keep)
+    _check(lib().idf_laplacian_decode_noalloc(C.byref(st), C.c_void_p(L_ptr), lrect[0], lrect[1], lrect[2],
+                                              lrect[3], lpitch, C.c_void_p(H_ptr), hrect[0], hrect[1], hrect[2],
+                                              hrect[3], hpitch, x0, y0, w, h, C.c_void_p(out_ptr), pitch,
+                                              _stream_ptr(stream)),
+           "idf_laplacian_decode_noalloc")

@@ -1,0 +1,62 @@
+"""The allocation-free Laplacian decode.
+
+Some callers cannot allocate device memory when they call the library (a
+plugin inside an engine that owns all device memory through its own pool, a
+frame loop that cannot take an allocation's latency).  For them
+idf_laplacian_decode_noalloc runs the decode with a fixed scratch array in
+the library's device image.  This file checks, through the C ABI, that it
+returns what idf_laplacian_decode returns, on two calls in a row (the second
+reuses the array the first left behind), and that a query too large for the
+fixed array is refused.  It is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _bands(idf, st, x0, y0, w, h, seed):
+    Lr, Hr = idf.laplacian_halo(st, x0, y0, w, h)
+    rng = np.random.default_rng(seed)
+    L = torch.from_numpy(rng.standard_normal((Lr[3], Lr[2])).astype(np.float32)).cuda()
+    H = torch.from_numpy(rng.standard_normal((Hr[3], Hr[2])).astype(np.float32)).cuda()
+    return Lr, Hr, L, H
+
+
+def test_noalloc_decode_matches_allocating_decode_twice():
+    import paper_2512_08309_gb300 as idf
+    idf.lib()
+    st = synth.config2_stack()
+    for call, (x0, y0, w, h) in enumerate([(-517, 2048, 700, 333), (4096, -77, 256, 1024)]):
+        Lr, Hr, L, H = _bands(idf, st, x0, y0, w, h, seed=call)
+        ref = torch.empty((h, w), device="cuda")
+        got = torch.full((h, w), float("nan"), device="cuda")
+        idf.laplacian_decode(st, L.data_ptr(), Lr, Lr[2], H.data_ptr(), Hr, Hr[2], x0, y0, w, h,
+                             ref.data_ptr(), w)
+        idf.laplacian_decode_noalloc(st, L.data_ptr(), Lr, Lr[2], H.data_ptr(), Hr, Hr[2], x0, y0, w, h,
+                                     got.data_ptr(), w)
+        torch.cuda.synchronize()
+        r, g = ref.cpu().numpy().astype(np.float64), got.cpu().numpy().astype(np.float64)
+        # the tolerance of the decode parity test (float32 arithmetic)
+        assert np.all(np.isfinite(g))
+        assert np.max(np.abs(g - r)) <= 1e-5 * np.max(np.abs(r))
+
+
+def test_noalloc_decode_rejects_queries_beyond_its_scratch():
+    import paper_2512_08309_gb300 as idf
+    idf.lib()
+    st = synth.config2_stack()
+    x0, y0, w, h = 0, 0, 8192, 8192
+    Lr, Hr = idf.laplacian_halo(st, x0, y0, w, h)
+    # buffers of the true sizes, so that nothing could be read out of bounds
+    L = torch.zeros((Lr[3], Lr[2]), device="cuda")
+    H = torch.zeros((Hr[3], Hr[2]), device="cuda")
+    out = torch.zeros((h, w), device="cuda")
+    with pytest.raises(idf.IdfError) as e:
+        idf.laplacian_decode_noalloc(st, L.data_ptr(), Lr, Lr[2], H.data_ptr(), Hr, Hr[2], x0, y0, w, h,
+                                     out.data_ptr(), w)
+    assert e.value.status == idf.IDF_EINVAL
