@@ -38,10 +38,13 @@ WORKLOAD = ("2-level hierarchy (coarse 64/128/128 @1/8, fine 64/128/256/256 + at
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="idf", choices=["idf", "reference"])
     p.add_argument("--query", type=int, default=QUERY)
+    p.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "fp32"])
+    p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
+    p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp32", action="store_true")
@@ -282,7 +285,8 @@ def run_idf(args, rank, world, local):
     torch.cuda.set_device(dev)
     st, wts = stack_and_weights()
     q = args.query
-    W = idf.World(0, st, wts, precision="bf16", device=local, profile=True)
+    W = idf.World(0, st, wts, precision=args.precision, device=local, profile=True,
+                  workspace_bytes=int(args.workspace_gb * (1 << 30)), cache_bytes=int(args.cache_gb * (1 << 30)))
     out = torch.empty((q, q), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -352,7 +356,7 @@ def run_idf(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "query": q, "steps_per_level": 20, "precision": "bf16",
+        "config": {"workload": WORKLOAD, "query": q, "steps_per_level": 20, "precision": args.precision,
                    "windows_per_step": {"coarse": wins[0] / args.steps, "fine": wins[1] / args.steps},
                    "cache": "emptied every step; working set of several GB per step exceeds L2",
                    "parallelism": f"{world} independent worlds" if world > 1 else "single GPU"},
@@ -384,7 +388,7 @@ def run_idf(args, rank, world, local):
     if not args.no_fp32 and rank == 0:
         nf, nc = window_counts(st, q)
         res = {}
-        for prec, nb in (("fp32", 8), ("bf16", 64)):
+        for prec, nb in (("fp32", 8), ("bf16", 64), ("bf16x3", 64)):
             Wp = idf.World(0, st, wts, precision=prec, max_batch=nb)
             t_lv = []
             for li, n_win in ((1, nb), (0, nb)):
@@ -407,7 +411,9 @@ def run_idf(args, rank, world, local):
                               "method": "FP32 SIMT UNet windows/s (idf_unet_forward) x windows per "
                                         "final px of this workload",
                               "bf16_same_method": res["bf16"]["px_s"],
+                              "bf16x3_same_method": res["bf16x3"]["px_s"],
                               "speedup_bf16_vs_fp32_unet": res["bf16"]["px_s"] / res["fp32"]["px_s"],
+                              "speedup_bf16x3_vs_fp32_unet": res["bf16x3"]["px_s"] / res["fp32"]["px_s"],
                               "detail": res}
     if not args.no_cpu and rank == 0 and world == 1:
         px, desc, threads, est = oracle_sample(seconds=15.0)

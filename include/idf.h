@@ -50,7 +50,13 @@ typedef enum {
   IDF_EUNSUPPORTED = 8   /* valid request that this build does not implement */
 } idf_status;
 
-typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2 } idf_precision;
+/* Arithmetic of the UNet convolutions.  IDF_FP32: float32 SIMT (the plain
+ * sampler).  IDF_BF16: bfloat16 operands on the tensor cores, float32
+ * accumulation, float32 residual stream.  IDF_BF16X3: the same tensor-core
+ * path with each operand split as hi + lo (both bfloat16) and the products
+ * hi*hi + lo*hi + hi*lo accumulated, which compensates the rounding of both
+ * operands at three times the tensor work.  IDF_FP8_E4M3 is not built yet. */
+typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2, IDF_BF16X3 = 3 } idf_precision;
 
 typedef enum {
   IDF_OUT_MODEL = 0,  /* the last level's final sample J_K in model units */

@@ -17,6 +17,10 @@
 //              tcgen05.commit; warps 2-5 wait for the accumulator, read it
 //              with tcgen05.ld (warp w reads TMEM lanes 32*(w%4)..+31) and
 //              write float32 NHWC output, adding the residual if given.
+//   Split:     with low parts given (IDF_BF16X3) every K slice runs three
+//              passes, A_hi B_hi + A_lo B_hi + A_hi B_lo, where x = hi + lo
+//              with hi = bf16(x), lo = bf16(x - hi): bfloat16 products with
+//              the rounding of both operands compensated.
 //   Waits:     every mbarrier wait is bounded (clock64 budget); on expiry
 //              the CTA sets the status word, drains what it issued and
 //              frees its TMEM before returning.
@@ -151,11 +155,14 @@ struct TcParams {
   float* y;
   int* status;
   int H, W, Cout, ks, n_kc, n_iter;
+  int split;  // 1: three passes per K slice, A_hi B_hi + A_lo B_hi + A_hi B_lo
 };
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB,
+                                                      const __grid_constant__ CUtensorMap tmA_lo,
+                                                      const __grid_constant__ CUtensorMap tmB_lo,
                                                       TcParams p) {
   constexpr int A_BYTES = BM * 128;
   constexpr int B_BYTES = BN * 128;
@@ -182,6 +189,8 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
   const int win = (int)(m0 / HW);
   const int y0 = (int)((m0 % HW) / p.W);
   const int pad = p.ks / 2;
+  const int passes = p.split ? 3 : 1;
+  const int n_total = p.n_iter * passes;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -195,6 +204,10 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
   if (warp == 0 && lane == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    if (p.split) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA_lo) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB_lo) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -212,17 +225,18 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
     if (lane == 0) {
       int last_issue[STAGES];
       for (int s = 0; s < STAGES; ++s) last_issue[s] = -1;
-      for (int it = 0; it < p.n_iter; ++it) {
+      for (int it = 0; it < n_total; ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
         if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true)) break;
-        const int tap = it / p.n_kc, kc = it % p.n_kc;
+        const int base = it / passes, pass = it % passes;
+        const int tap = base / p.n_kc, kc = base % p.n_kc;
         const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
         uint8_t* a = smem + (size_t)s * STAGE_BYTES;
         uint8_t* b = a + A_BYTES;
         mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-        tma_load_4d(a, &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
-        tma_load_2d(b, &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
+        tma_load_4d(a, pass == 1 ? &tmA_lo : &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
+        tma_load_2d(b, pass == 2 ? &tmB_lo : &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
         last_issue[s] = it;
       }
       if (*abort_flag) {
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      for (int it = 0; it < p.n_iter; ++it) {
+      for (int it = 0; it < n_total; ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
         if (!wait_bar(&full_bar[s], ph, abort_flag, p.status, true)) break;
@@ -303,8 +317,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <int BN, int STAGES>
-bool launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, dim3 grid, cudaStream_t st,
-            std::string* err) {
+bool launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, const CUtensorMap& blo,
+            const TcParams& p, dim3 grid, cudaStream_t st, std::string* err) {
   const size_t smem = (size_t)STAGES * (BM * 128 + BN * 128) + 1024;
   static bool attr = false;
   if (!attr) {
@@ -315,7 +329,7 @@ bool launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, dim3 
     }
     attr = true;
   }
-  conv_tc_kernel<BN, STAGES><<<grid, 192, smem, st>>>(a, b, p);
+  conv_tc_kernel<BN, STAGES><<<grid, 192, smem, st>>>(a, b, alo, blo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -335,8 +349,9 @@ bool conv_tc_shape_ok(int H, int W) {
   return W >= 1 && W <= 128 && 128 % W == 0 && ((int64_t)H * W) % 128 == 0 && 128 / W <= H;
 }
 
-bool conv_tc_forward(const bf16* x, const bf16* w, const float* res, float* y, int n, int H, int W,
-                     int Cin, int Cout, int ks, int* status, cudaStream_t st, std::string* err) {
+bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16* w_lo, const float* res,
+                     float* y, int n, int H, int W, int Cin, int Cout, int ks, int* status, cudaStream_t st,
+                     std::string* err) {
   if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
     *err = "shape not supported by the tensor-core convolution";
     return false;
@@ -347,7 +362,30 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const float* res, float* y, i
     return false;
   }
   const int BN = Cout <= 256 ? Cout : 256;
-  CUtensorMap ta, tb;
+  const bool split = x_lo && w_lo;
+  CUtensorMap ta, tb, ta_lo, tb_lo;
+  auto encA = [&](CUtensorMap* m, const bf16* ptr) {
+    cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    cuuint32_t box[4] = {64, (cuuint32_t)W, (cuuint32_t)(128 / W), 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)ptr, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  auto encB = [&](CUtensorMap* m, const bf16* ptr) {
+    cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)ks * ks * Cout};
+    cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)BN};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (split && (!encA(&ta_lo, x_lo) || !encB(&tb_lo, w_lo))) {
+    *err = "tensor map (low parts) encode failed";
+    return false;
+  }
   {
     cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
     cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
@@ -384,12 +422,17 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const float* res, float* y, i
   p.ks = ks;
   p.n_kc = Cin / 64;
   p.n_iter = ks * ks * (Cin / 64);
+  p.split = split ? 1 : 0;
+  if (!split) {
+    ta_lo = ta;
+    tb_lo = tb;
+  }
   const int64_t M = (int64_t)n * H * W;
   dim3 grid((unsigned)(M / BM), (unsigned)(Cout / BN));
   switch (BN) {
-    case 64: return launch<64, 4>(ta, tb, p, grid, st, err);
-    case 128: return launch<128, 3>(ta, tb, p, grid, st, err);
-    case 256: return launch<256, 2>(ta, tb, p, grid, st, err);
+    case 64: return launch<64, 4>(ta, tb, ta_lo, tb_lo, p, grid, st, err);
+    case 128: return launch<128, 3>(ta, tb, ta_lo, tb_lo, p, grid, st, err);
+    case 256: return launch<256, 2>(ta, tb, ta_lo, tb_lo, p, grid, st, err);
     default:
       *err = "unsupported N tile";
       return false;

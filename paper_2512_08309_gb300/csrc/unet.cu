@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const Tin* __restrict__ 
                                                         const float* __restrict__ wk,
                                                         const Tout* __restrict__ res,
                                                         Tout* __restrict__ y, int n, int H, int W,
-                                                        int Cin, int Cout) {
+                                                        int Cin, int Cout,
+                                                        const Tin* __restrict__ xlo = nullptr) {
   __shared__ float As[CBK][CBM + 4];
   __shared__ float Bs[CBK][CBN];
   const int tid = threadIdx.x;
@@ -99,8 +100,11 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const Tin* __restrict__ 
       if (a_ok[i] && k < K) {
         const int tap = k / Cin, ci = k - tap * Cin;
         const int sy = a_py[i] + tap / KS - KS / 2, sx = a_px[i] + tap % KS - KS / 2;
-        if (sy >= 0 && sy < H && sx >= 0 && sx < W)
-          v = ld<Tin>(x + (((int64_t)a_b[i] * H + sy) * W + sx) * Cin + ci);
+        if (sy >= 0 && sy < H && sx >= 0 && sx < W) {
+          const int64_t off = (((int64_t)a_b[i] * H + sy) * W + sx) * Cin + ci;
+          v = ld<Tin>(x + off);
+          if (xlo) v += ld<Tin>(xlo + off);
+        }
       }
       As[kk][mm] = v;
     }
@@ -192,7 +196,8 @@ __global__ void __launch_bounds__(256) gn_stats_kernel(const T* __restrict__ x, 
 template <typename Tin, typename Tout, bool SILU>
 __global__ void gn_apply_kernel(const Tin* __restrict__ x, const float2* __restrict__ stats,
                                 int64_t n_el, int HW, int C, int G, Tout* __restrict__ y,
-                                Tout* __restrict__ copy) {
+                                Tout* __restrict__ copy, Tout* __restrict__ ylo,
+                                Tout* __restrict__ copylo) {
   const int Cg = C / G;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_el;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -204,6 +209,8 @@ __global__ void gn_apply_kernel(const Tin* __restrict__ x, const float2* __restr
     if (SILU) v = v / (1.0f + expf(-v));
     st<Tout>(y + i, v);
     if (copy) st<Tout>(copy + i, xv);
+    if (ylo) st<Tout>(ylo + i, v - ld<Tout>(y + i));
+    if (copylo) st<Tout>(copylo + i, xv - ld<Tout>(copy + i));
   }
 }
 
@@ -308,7 +315,9 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
                                                         const float2* __restrict__ stats,
                                                         int n_units, int units_per_win, int C,
                                                         int G, TA* __restrict__ y,
-                                                        TA* __restrict__ copy) {
+                                                        TA* __restrict__ copy,
+                                                        TA* __restrict__ ylo,
+                                                        TA* __restrict__ copylo) {
   const int C8 = C / 8, Cg = C / G;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
     const int b = u / units_per_win;
@@ -326,6 +335,17 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
     }
     Pack8<TA>::store(y + (int64_t)u * 8, v);
     if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+    if (ylo) {
+      // low parts: what bfloat16 rounding of the high parts left out
+      float r[8], rc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        r[j] = v[j] - __bfloat162float(__float2bfloat16_rn(v[j]));
+        rc[j] = xv[j] - __bfloat162float(__float2bfloat16_rn(xv[j]));
+      }
+      Pack8<TA>::store(ylo + (int64_t)u * 8, r);
+      if (copylo) Pack8<TA>::store(copylo + (int64_t)u * 8, rc);
+    }
   }
 }
 
@@ -391,7 +411,7 @@ template <typename TA>
 __global__ void __launch_bounds__(256) conv_out_kernel(const TA* __restrict__ x,
                                                        const float* __restrict__ wk,
                                                        float* __restrict__ y, int n, int H, int W,
-                                                       int Cin) {
+                                                       int Cin, const TA* __restrict__ xlo) {
   extern __shared__ float wsm[];  // [9][Cin]
   for (int i = threadIdx.x; i < 9 * Cin; i += blockDim.x) wsm[i] = wk[i];
   __syncthreads();
@@ -411,6 +431,12 @@ __global__ void __launch_bounds__(256) conv_out_kernel(const TA* __restrict__ x,
       for (int c = 0; c < Cin; c += 8) {
         float v[8];
         Load8<TA>::load(xp + c, v);
+        if (xlo) {
+          float vl[8];
+          Load8<TA>::load(xlo + ((b * H + sy) * W + sx) * Cin + c, vl);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] += vl[j];
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc = fmaf(v[j], wp[c + j], acc);
       }
@@ -423,7 +449,7 @@ __global__ void __launch_bounds__(256) conv_out_kernel(const TA* __restrict__ x,
 // registers; keys and values of the head are staged in shared memory.
 template <typename T, int D>
 __global__ void attention_d_kernel(const float* __restrict__ qkv, int Tn, int C, int heads,
-                                   T* __restrict__ out) {
+                                   T* __restrict__ out, T* __restrict__ out_lo) {
   extern __shared__ float sm[];
   const int b = blockIdx.x / heads, h = blockIdx.x % heads;
   float* Ks = sm;
@@ -479,6 +505,14 @@ __global__ void attention_d_kernel(const float* __restrict__ qkv, int Tn, int C,
     T* op = out + ((int64_t)b * Tn + t) * C + h * D;
 #pragma unroll
     for (int c = 0; c < D; ++c) st<T>(op + c, o[c] * inv);
+    if (out_lo) {
+      T* ol = out_lo + ((int64_t)b * Tn + t) * C + h * D;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const float v = o[c] * inv;
+        st<T>(ol + c, v - ld<T>(op + c));
+      }
+    }
   }
 }
 
@@ -571,14 +605,16 @@ __global__ void attention_kernel(const float* __restrict__ qkv, int Tn, int C, i
 }
 
 // ------------------------------------------------------------ engine
-bool conv_tc_forward(const bf16* x, const bf16* w, const float* res, float* y, int n, int H, int W,
-                     int Cin, int Cout, int ks, int* status, cudaStream_t st, std::string* err);
+bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16* w_lo, const float* res,
+                     float* y, int n, int H, int W, int Cin, int Cout, int ks, int* status, cudaStream_t st,
+                     std::string* err);
 bool conv_tc_shape_ok(int H, int W);
 
 struct ConvW {
   int cin = 0, cout = 0, ks = 0;
   float* w32 = nullptr;  // [K][Cout], k = tap*Cin + ci
   bf16* w16 = nullptr;   // [tap][Cout][Cin] (tensor-core layout) or null
+  bf16* w16lo = nullptr; // low parts of the same (IDF_BF16X3) or null
   bool tc = false;
 };
 
@@ -596,11 +632,15 @@ struct LevelBufs {
   void* T2 = nullptr;
   void* T3 = nullptr;
   void* T4 = nullptr;
+  void* T1lo = nullptr;  // low parts of T1, T4 and of the attention output (IDF_BF16X3)
+  void* T4lo = nullptr;
+  void* T3lo = nullptr;
 };
 
 struct UNet {
   UNetDesc d;
   int precision = 0;
+  bool split = false;   // IDF_BF16X3
   int max_batch = 0;
   std::vector<ConvW> convs;
   std::vector<LevelBufs> lv;
@@ -648,13 +688,15 @@ static size_t level_cmax(const UNetDesc& d, int l) {
   return c;
 }
 
-// six float32 buffers and two operand buffers per resolution level
+// six float32 buffers and two operand buffers per resolution level (plus
+// three low-part buffers with IDF_BF16X3)
 size_t unet_bytes_per_window(const UNetDesc& d, int precision) {
-  const size_t ea = precision == 1 ? 2 : 4;
+  const size_t ea = (precision == 1 || precision == 3) ? 2 : 4;
+  const size_t nlo = precision == 3 ? 3 : 0;
   size_t t = 0;
   for (int l = 0; l < d.levels; ++l) {
     const size_t H = (size_t)(d.window >> l);
-    t += (6 * 4 + 2 * ea) * H * H * level_cmax(d, l);
+    t += (6 * 4 + (2 + nlo) * ea) * H * H * level_cmax(d, l);
   }
   return t + (size_t)GN_MAX_CHUNKS * d.groups * sizeof(double2);
 }
@@ -674,10 +716,12 @@ void unet_destroy(UNet* u) {
   for (auto& c : u->convs) {
     cudaFree(c.w32);
     cudaFree(c.w16);
+    cudaFree(c.w16lo);
   }
   for (auto& b : u->lv) {
     cudaFree(b.P); cudaFree(b.SK); cudaFree(b.CAT); cudaFree(b.M);
     cudaFree(b.T1); cudaFree(b.T2); cudaFree(b.T3); cudaFree(b.T4);
+    cudaFree(b.T1lo); cudaFree(b.T4lo); cudaFree(b.T3lo);
   }
   cudaFree(u->stats);
   cudaFree(u->gnpart);
@@ -689,7 +733,9 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
   UNet* u = new UNet();
   u->d = d;
   u->precision = precision;
+  u->split = precision == 3;
   u->max_batch = std::max(1, max_batch);
+  const bool bfm = precision == 1 || precision == 3;
   auto shapes = unet_param_shapes(d);
   size_t off = 0;
   // resolution of each conv, to know whether the tensor-core kernel applies
@@ -708,16 +754,23 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
           pk[((size_t)t * c.cin + ci) * c.cout + o] = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
     if (!ck(cudaMalloc(&c.w32, pk.size() * 4), err, "cudaMalloc weights")) { unet_destroy(u); return nullptr; }
     if (!ck(cudaMemcpy(c.w32, pk.data(), pk.size() * 4, cudaMemcpyHostToDevice), err, "copy weights")) { unet_destroy(u); return nullptr; }
-    if (precision == 1 && conv_tc_supported(c.cin, c.cout, c.ks)) {
-      // (Cout, Cin, kh, kw) -> [tap][Cout][Cin] bfloat16
-      std::vector<bf16> p16((size_t)taps * c.cout * c.cin);
+    if (bfm && conv_tc_supported(c.cin, c.cout, c.ks)) {
+      // (Cout, Cin, kh, kw) -> [tap][Cout][Cin] bfloat16 (and the low parts)
+      std::vector<bf16> p16((size_t)taps * c.cout * c.cin), p16lo(p16.size());
       for (int o = 0; o < c.cout; ++o)
         for (int ci = 0; ci < c.cin; ++ci)
-          for (int t = 0; t < taps; ++t)
-            p16[((size_t)t * c.cout + o) * c.cin + ci] =
-                __float2bfloat16_rn(w_host[off + ((size_t)o * c.cin + ci) * taps + t]);
+          for (int t = 0; t < taps; ++t) {
+            const float v = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
+            const bf16 hi = __float2bfloat16_rn(v);
+            p16[((size_t)t * c.cout + o) * c.cin + ci] = hi;
+            p16lo[((size_t)t * c.cout + o) * c.cin + ci] = __float2bfloat16_rn(v - __bfloat162float(hi));
+          }
       if (!ck(cudaMalloc(&c.w16, p16.size() * 2), err, "cudaMalloc bf16 weights")) { unet_destroy(u); return nullptr; }
       if (!ck(cudaMemcpy(c.w16, p16.data(), p16.size() * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")) { unet_destroy(u); return nullptr; }
+      if (u->split) {
+        if (!ck(cudaMalloc(&c.w16lo, p16lo.size() * 2), err, "cudaMalloc bf16 weights")) { unet_destroy(u); return nullptr; }
+        if (!ck(cudaMemcpy(c.w16lo, p16lo.data(), p16lo.size() * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")) { unet_destroy(u); return nullptr; }
+      }
       c.tc = true;
     }
     off += (size_t)c.cout * c.cin * taps;
@@ -729,10 +782,11 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
     b.H = d.window >> l;
     b.cmax = level_cmax(d, l);
     const size_t bytes = B * b.H * b.H * b.cmax * 4;
-    const size_t obytes = B * b.H * b.H * b.cmax * (precision == 1 ? 2 : 4);
-    void** ps[8] = {&b.P, &b.SK, &b.CAT, &b.M, &b.T2, &b.T3, &b.T1, &b.T4};
+    const size_t obytes = B * b.H * b.H * b.cmax * (bfm ? 2 : 4);
+    void** ps[11] = {&b.P, &b.SK, &b.CAT, &b.M, &b.T2, &b.T3, &b.T1, &b.T4, &b.T1lo, &b.T4lo, &b.T3lo};
+    const int nbuf = u->split ? 11 : 8;
     bool ok = true;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < nbuf; ++i)
       if (ok && !ck(cudaMalloc(ps[i], i < 6 ? bytes : obytes), err, "cudaMalloc UNet workspace")) ok = false;
     u->lv.push_back(b);
     if (!ok) { unet_destroy(u); return nullptr; }
@@ -761,7 +815,8 @@ struct Ctx {
 
 // out (float32) = conv(x) (+ res), x in operand type TA (or float32 x_f32)
 template <typename TA>
-void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H) {
+void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H,
+              const void* x_lo = nullptr) {
   if (!c.ok) return;
   const int W = H;
   const double flops = 2.0 * c.n * H * W * (double)w.cout * w.ks * w.ks * w.cin;
@@ -770,7 +825,8 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     // algorithmic bytes: bf16 operand read once, weights, float32 output (+ residual)
     const double by = c.n * H * W * (2.0 * w.cin + 4.0 * w.cout * (res ? 2 : 1)) + 2.0 * w.ks * w.ks * w.cin * w.cout;
     const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
-    const bool ok = conv_tc_forward((const bf16*)x, w.w16, res, y, c.n, H, W, w.cin, w.cout, w.ks,
+    const bool ok = conv_tc_forward((const bf16*)x, w.w16, c.u->split ? (const bf16*)x_lo : nullptr,
+                                    c.u->split ? w.w16lo : nullptr, res, y, c.n, H, W, w.cin, w.cout, w.ks,
                          c.u->status, c.st, &e);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     if (!ok) {
@@ -792,7 +848,7 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     return;
   }
   if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 8 == 0) {
-    conv_out_kernel<TA><<<grid1d(M, 256), 256, 9 * w.cin * sizeof(float), c.st>>>((const TA*)x, w.w32, y, c.n, H, W, w.cin);
+    conv_out_kernel<TA><<<grid1d(M, 256), 256, 9 * w.cin * sizeof(float), c.st>>>((const TA*)x, w.w32, y, c.n, H, W, w.cin, (const TA*)x_lo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
     return;
@@ -800,10 +856,10 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
   dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((w.cout + CBN - 1) / CBN));
   if (w.ks == 3) {
     if (x_f32) conv_simt_kernel<3, float, float><<<grid, 256, 0, c.st>>>((const float*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
-    else conv_simt_kernel<3, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
+    else conv_simt_kernel<3, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout, (const TA*)x_lo);
   } else {
     if (x_f32) conv_simt_kernel<1, float, float><<<grid, 256, 0, c.st>>>((const float*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
-    else conv_simt_kernel<1, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout);
+    else conv_simt_kernel<1, TA, float><<<grid, 256, 0, c.st>>>((const TA*)x, w.w32, res, y, c.n, H, W, w.cin, w.cout, (const TA*)x_lo);
   }
   if (c.u->prof) c.u->prof->end(pr, c.st);
   c.u->launches++;
@@ -811,7 +867,8 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
 
 // y (TA) = silu(gn(x)) or gn(x); copy (TA, optional) = x
 template <typename TA>
-void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = nullptr) {
+void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = nullptr,
+        void* ylo = nullptr, void* copylo = nullptr) {
   if (!c.ok) return;
   const int G = c.u->d.groups;
   const double nb = (double)c.n * H * H * C;
@@ -834,9 +891,9 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
     gn_finalize_kernel<<<(c.n * G + 127) / 128, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
     const int upw = HW * (C / 8);
     if (silu)
-      gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy);
+      gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
     else
-      gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy);
+      gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches += 3;
     return;
@@ -844,9 +901,9 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
   gn_stats_kernel<float><<<c.n * G, 256, 0, c.st>>>(x, H * H, C, G, c.u->stats);
   const int64_t nel = (int64_t)c.n * H * H * C;
   if (silu)
-    gn_apply_kernel<float, TA, true><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy);
+    gn_apply_kernel<float, TA, true><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
   else
-    gn_apply_kernel<float, TA, false><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy);
+    gn_apply_kernel<float, TA, false><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
   if (c.u->prof) c.u->prof->end(pr, c.st);
   c.u->launches += 2;
 }
@@ -859,16 +916,18 @@ void resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
   const ConvW* sk = nullptr;
   if (cin != cout) sk = &c.u->convs[wi++];
   const bool need_copy = sk && !std::is_same<TA, float>::value;
-  gn<TA>(c, X, b.H, cin, b.T1, true, need_copy ? b.T4 : nullptr);
-  conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H);
+  const bool sp = c.u->split;
+  gn<TA>(c, X, b.H, cin, b.T1, true, need_copy ? b.T4 : nullptr, sp ? b.T1lo : nullptr,
+         sp && need_copy ? b.T4lo : nullptr);
+  conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H, sp ? b.T1lo : nullptr);
   const float* res = X;
   if (sk) {
-    if (need_copy) conv_run<TA>(c, *sk, b.T4, false, nullptr, (float*)b.T3, b.H);
+    if (need_copy) conv_run<TA>(c, *sk, b.T4, false, nullptr, (float*)b.T3, b.H, sp ? b.T4lo : nullptr);
     else conv_run<TA>(c, *sk, X, true, nullptr, (float*)b.T3, b.H);
     res = (const float*)b.T3;
   }
-  gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true);
-  conv_run<TA>(c, c2, b.T1, false, res, Y, b.H);
+  gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true, nullptr, sp ? b.T1lo : nullptr);
+  conv_run<TA>(c, c2, b.T1, false, res, Y, b.H, sp ? b.T1lo : nullptr);
 }
 
 template <typename TA>
@@ -894,22 +953,24 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   if (d.attn) {
     const ConvW& qkv = u->convs[wi++];
     const ConvW& proj = u->convs[wi++];
-    gn<TA>(c, cur, bl.H, prev, bl.T1, false);
-    conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H);
+    gn<TA>(c, cur, bl.H, prev, bl.T1, false, nullptr, u->split ? bl.T1lo : nullptr);
+    conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H, u->split ? bl.T1lo : nullptr);
     const int Tn = bl.H * bl.H, dh = prev / d.heads;
     const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
     const int pr = u->prof ? u->prof->begin(PK_ATTENTION, st, 4.0 * n * (double)Tn * Tn * prev, 0.0) : -1;
     if (dh == 64 || dh == 32 || dh == 16) {
       auto kern = dh == 64 ? attention_d_kernel<TA, 64> : dh == 32 ? attention_d_kernel<TA, 32> : attention_d_kernel<TA, 16>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3);
+      kern<<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3,
+                                                         u->split ? (TA*)bl.T3lo : nullptr);
     } else {
       cudaFuncSetAttribute(attention_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attention_kernel<TA><<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3);
+      if (u->split) cudaMemsetAsync(bl.T3lo, 0, (size_t)n * Tn * prev * sizeof(TA), st);
     }
     if (u->prof) u->prof->end(pr, st);
     u->launches++;
-    conv_run<TA>(c, proj, bl.T3, false, cur, (float*)bl.CAT, bl.H);
+    conv_run<TA>(c, proj, bl.T3, false, cur, (float*)bl.CAT, bl.H, u->split ? bl.T3lo : nullptr);
     cur = (const float*)bl.CAT;
   }
   resblock<TA>(c, wi, bl, cur, prev, prev, (float*)bl.M);
@@ -922,8 +983,8 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     prev = d.ch[l];
   }
   LevelBufs& b0 = u->lv[0];
-  gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true);
-  conv_run<TA>(c, u->convs[wi++], b0.T1, false, nullptr, F, d.window);
+  gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true, nullptr, u->split ? b0.T1lo : nullptr);
+  conv_run<TA>(c, u->convs[wi++], b0.T1, false, nullptr, F, d.window, u->split ? b0.T1lo : nullptr);
   if (c.ok) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -944,7 +1005,7 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
     return false;
   }
   if (n <= 0) return true;
-  if (u->precision == 1) return forward_t<bf16>(u, x_in, n, F, st, err);
+  if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err);
   return forward_t<float>(u, x_in, n, F, st, err);
 }
 

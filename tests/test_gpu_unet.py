@@ -65,3 +65,13 @@ def test_config2_unet_bf16(idf, li):
     print(f"level {li}: rms {rms / ref.std():.3e} sigma, max {np.max(np.abs(d)) / ref.std():.3e} sigma")
     assert rms <= 1.5e-2 * ref.std()
     assert np.max(np.abs(d)) <= 6e-2 * ref.std()
+
+
+@pytest.mark.parametrize("li", [0, 1])
+def test_config2_unet_bf16x3(idf, li):
+    # hi/lo split of both operands: the remaining error is the dropped lo*lo
+    # product and the low parts' own rounding, about 2^-16 relative
+    got, ref = run(idf, synth.config2_stack(), li, "bf16x3", 2, seed=li)
+    err = np.max(np.abs(got - ref))
+    print(f"level {li}: bf16x3 max {err / ref.std():.3e} sigma")
+    assert err <= 1e-3 * ref.std()
