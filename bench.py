@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "fp32"])
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
+    p.add_argument("--profile-unet", type=int, default=0,
+                   help="profiling mode: one warm-up and one timed fine-level UNet forward on N windows")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp32", action="store_true")
@@ -424,8 +426,35 @@ def run_idf(args, rank, world, local):
     return 0
 
 
+def run_profile_unet(args):
+    """Small-footprint profiling case: the fine UNet of the 2-level stack on
+    N 128x128 windows (about 80 kernel launches per forward)."""
+    import torch
+
+    import paper_2512_08309_gb300 as idf
+    st, wts = stack_and_weights()
+    n = args.profile_unet
+    W = idf.World(0, st, wts, precision=args.precision, max_batch=n, cache_bytes=64 << 20, profile=True)
+    x = torch.randn((n, 2, 128, 128), device="cuda")
+    y = torch.empty((n, 1, 128, 128), device="cuda")
+    W.unet_forward(1, x.data_ptr(), n, y.data_ptr())
+    torch.cuda.synchronize()
+    s0 = W.stats()
+    W.unet_forward(1, x.data_ptr(), n, y.data_ptr())
+    torch.cuda.synchronize()
+    s1 = W.stats()
+    prof = {k: {f: s1["profile"][k][f] - s0["profile"][k][f] for f in ("launches", "ms", "flops")}
+            for k in s1["profile"] if s1["profile"][k]["launches"] - s0["profile"][k]["launches"]}
+    print(json.dumps({"profile_unet": n, "precision": args.precision, "kernels": prof,
+                      "finite": bool(torch.isfinite(y).all().item())}))
+    W.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_unet:
+        return run_profile_unet(args)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)

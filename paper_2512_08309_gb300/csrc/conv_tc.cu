@@ -12,15 +12,18 @@
 //              -- and a 2-D TMA box of the weights (64 channels x BN rows).
 //              Both land in shared memory in the 128-byte swizzled K-major
 //              layout that the UMMA descriptors describe.
-//   Warps:     warp 0 lane 0 issues TMA; warp 1 allocates TMEM and lane 0
-//              issues tcgen05.mma (M=128, N=BN, K=16, four per stage) and
-//              tcgen05.commit; warps 2-5 wait for the accumulator, read it
-//              with tcgen05.ld (warp w reads TMEM lanes 32*(w%4)..+31) and
-//              write float32 NHWC output, adding the residual if given.
-//   Split:     with low parts given (IDF_BF16X3) every K slice runs three
-//              passes, A_hi B_hi + A_lo B_hi + A_hi B_lo, where x = hi + lo
-//              with hi = bf16(x), lo = bf16(x - hi): bfloat16 products with
-//              the rounding of both operands compensated.
+//   Warps:     persistent CTAs, one per SM.  Warp 0 lane 0 issues TMA into a
+//              ring of stages; warp 1 allocates 2 x BN TMEM columns and lane
+//              0 issues tcgen05.mma (M=128, N=BN, K=16, four per stage) into
+//              one of two accumulators and tcgen05.commit; warps 2-5 read the
+//              other accumulator with tcgen05.ld (warp w reads TMEM lanes
+//              32*(w%4)..+31) and write float32 NHWC output, adding the
+//              residual if given, while the next tile accumulates.
+//   Split:     with low parts given (IDF_BF16X3) a stage holds A_hi, A_lo,
+//              B_hi and B_lo and issues A_hi B_hi + A_lo B_hi + A_hi B_lo per
+//              K step, where x = hi + lo with hi = bf16(x), lo = bf16(x - hi):
+//              bfloat16 products with the rounding of both operands
+//              compensated.
 //   Waits:     every mbarrier wait is bounded (clock64 budget); on expiry
 //              the CTA sets the status word, drains what it issued and
 //              frees its TMEM before returning.
@@ -155,56 +158,67 @@ struct TcParams {
   float* y;
   int* status;
   int H, W, Cout, ks, n_kc, n_iter;
-  int split;  // 1: three passes per K slice, A_hi B_hi + A_lo B_hi + A_hi B_lo
+  int m_tiles, n_tiles;  // output tiles: 128-pixel rows x BN channels
 };
 
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB,
-                                                      const __grid_constant__ CUtensorMap tmA_lo,
-                                                      const __grid_constant__ CUtensorMap tmB_lo,
-                                                      TcParams p) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent kernel: CTA c handles tiles c, c + gridDim.x, ... (channel tiles
+// of the same pixel tile are adjacent, so they share the activation tile in
+// L2).  The shared-memory ring of STAGES stages runs across tile boundaries;
+// two TMEM accumulators (2 x BN columns) let the epilogue of one tile overlap
+// the main loop of the next.
+template <int BN, int STAGES, bool SPLIT>
+__global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB,
+                                                         const __grid_constant__ CUtensorMap tmA_lo,
+                                                         const __grid_constant__ CUtensorMap tmB_lo,
+                                                         TcParams p) {
   constexpr int A_BYTES = BM * 128;
   constexpr int B_BYTES = BN * 128;
-  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int NP = SPLIT ? 2 : 1;                  // hi (and lo) parts per operand
+  constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
+  __shared__ int skip_sh;
   uint8_t* smem = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
   volatile int* abort_flag = &abort_sh;
   // once any CTA of any launch has given up on a wait, later CTAs return at
   // once (one thread reads the status so that the whole CTA decides alike)
-  __shared__ int skip_sh;
   if (threadIdx.x == 0) skip_sh = *(volatile int*)p.status;
   __syncthreads();
   if (skip_sh) return;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t m0 = (int64_t)blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;
   const int64_t HW = (int64_t)p.H * p.W;
-  const int win = (int)(m0 / HW);
-  const int y0 = (int)((m0 % HW) / p.W);
   const int pad = p.ks / 2;
-  const int passes = p.split ? 3 : 1;
-  const int n_total = p.n_iter * passes;
+  const int n_tiles = p.m_tiles * p.n_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 128);
+    }
+    mbar_init(&drain_bar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0 && lane == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
-    if (p.split) {
+    if (SPLIT) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA_lo) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB_lo) : "memory");
     }
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
-                 "r"(BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -225,19 +239,33 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
     if (lane == 0) {
       int last_issue[STAGES];
       for (int s = 0; s < STAGES; ++s) last_issue[s] = -1;
-      for (int it = 0; it < n_total; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true)) break;
-        const int base = it / passes, pass = it % passes;
-        const int tap = base / p.n_kc, kc = base % p.n_kc;
-        const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
-        uint8_t* a = smem + (size_t)s * STAGE_BYTES;
-        uint8_t* b = a + A_BYTES;
-        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-        tma_load_4d(a, pass == 1 ? &tmA_lo : &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
-        tma_load_2d(b, pass == 2 ? &tmB_lo : &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
-        last_issue[s] = it;
+      uint32_t it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t m0 = (int64_t)(tile / p.n_tiles) * BM;
+        const int n0 = (tile % p.n_tiles) * BN;
+        const int win = (int)(m0 / HW);
+        const int y0 = (int)((m0 % HW) / p.W);
+        for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true)) {
+            ok = false;
+            break;
+          }
+          const int tap = kk / p.n_kc, kc = kk % p.n_kc;
+          const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
+          uint8_t* a = smem + (size_t)s * STAGE_BYTES;
+          uint8_t* b = a + NP * A_BYTES;
+          mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+          tma_load_4d(a, &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
+          tma_load_2d(b, &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
+          if (SPLIT) {
+            tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * 64, dx, y0 + dy, win);
+            tma_load_2d(b + B_BYTES, &tmB_lo, &full_bar[s], kc * 64, tap * p.Cout + n0);
+          }
+          last_issue[s] = (int)it;
+        }
       }
       if (*abort_flag) {
         // drain the copies this thread issued before leaving
@@ -249,31 +277,54 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      for (int it = 0; it < n_total; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!wait_bar(&full_bar[s], ph, abort_flag, p.status, true)) break;
+      uint32_t it = 0, acc = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++acc) {
+        const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
+        if (!wait_bar(&acce_bar[buf], aph ^ 1u, abort_flag, p.status, true)) break;
         fence_after();
-        const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
-        const uint32_t b = a + A_BYTES;
+        const uint32_t d = tmem + buf * BN;
+        for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!wait_bar(&full_bar[s], ph, abort_flag, p.status, true)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
+          const uint32_t b = a + NP * A_BYTES;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_bf16(tmem, umma_desc(a + 32 * k), umma_desc(b + 32 * k), idesc,
-                   (it > 0 || k > 0) ? 1u : 0u);
-        mma_commit(&empty_bar[s]);
+          for (int k = 0; k < 4; ++k) {
+            mma_bf16(d, umma_desc(a + 32 * k), umma_desc(b + 32 * k), idesc, (kk > 0 || k > 0) ? 1u : 0u);
+            if (SPLIT) {
+              mma_bf16(d, umma_desc(a + A_BYTES + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
+              mma_bf16(d, umma_desc(a + 32 * k), umma_desc(b + B_BYTES + 32 * k), idesc, 1u);
+            }
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        if (!ok) break;
+        mma_commit(&accf_bar[buf]);
       }
-      mma_commit(&acc_bar);
+      // every MMA this thread issued has completed once this commit arrives
+      mma_commit(&drain_bar);
+      wait_bar(&drain_bar, 0, abort_flag, p.status, false);
     }
   } else {
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    const int64_t m = m0 + row;
-    if (wait_bar(&acc_bar, 0, abort_flag, p.status, true)) {
+    uint32_t acc = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++acc) {
+      const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
+      if (!wait_bar(&accf_bar[buf], aph, abort_flag, p.status, true)) break;
       fence_after();
+      const int64_t m = (int64_t)(tile / p.n_tiles) * BM + row;
+      const int n0 = (tile % p.n_tiles) * BN;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        tmem_ld32(tmem + buf * BN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
         float* yp = p.y + m * p.Cout + n0 + c0;
         const float* rp = p.res ? p.res + m * p.Cout + n0 + c0 : nullptr;
 #pragma unroll
@@ -287,18 +338,16 @@ __global__ void __launch_bounds__(192) conv_tc_kernel(const __grid_constant__ CU
           reinterpret_cast<float4*>(yp)[j] = v;
         }
       }
+      fence_before();
+      mbar_arrive(&acce_bar[buf]);
     }
   }
   fence_before();
   __syncthreads();
   if (warp == 1) {
-    if (*abort_flag && lane == 0) {
-      // the last commit tracks every MMA issued; wait for it before freeing TMEM
-      wait_bar(&acc_bar, 0, abort_flag, p.status, false);
-    }
     __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
                  : "memory");
   }
 }
@@ -316,20 +365,32 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int BN, int STAGES>
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int BN, int STAGES, bool SPLIT>
 bool launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, const CUtensorMap& blo,
-            const TcParams& p, dim3 grid, cudaStream_t st, std::string* err) {
-  const size_t smem = (size_t)STAGES * (BM * 128 + BN * 128) + 1024;
+            const TcParams& p, cudaStream_t st, std::string* err) {
+  const size_t smem = (size_t)STAGES * (SPLIT ? 2 : 1) * (BM * 128 + BN * 128) + 1024;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
       *err = "cudaFuncSetAttribute failed";
       return false;
     }
     attr = true;
   }
-  conv_tc_kernel<BN, STAGES><<<grid, 192, smem, st>>>(a, b, alo, blo, p);
+  const int tiles = p.m_tiles * p.n_tiles;
+  const int grid = tiles < sm_count() ? tiles : sm_count();
+  conv_tc_kernel<BN, STAGES, SPLIT><<<grid, 192, smem, st>>>(a, b, alo, blo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -422,21 +483,28 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
   p.ks = ks;
   p.n_kc = Cin / 64;
   p.n_iter = ks * ks * (Cin / 64);
-  p.split = split ? 1 : 0;
+  p.m_tiles = (int)((int64_t)n * H * W / BM);
+  p.n_tiles = Cout / BN;
   if (!split) {
     ta_lo = ta;
     tb_lo = tb;
   }
-  const int64_t M = (int64_t)n * H * W;
-  dim3 grid((unsigned)(M / BM), (unsigned)(Cout / BN));
-  switch (BN) {
-    case 64: return launch<64, 4>(ta, tb, ta_lo, tb_lo, p, grid, st, err);
-    case 128: return launch<128, 3>(ta, tb, ta_lo, tb_lo, p, grid, st, err);
-    case 256: return launch<256, 2>(ta, tb, ta_lo, tb_lo, p, grid, st, err);
-    default:
-      *err = "unsupported N tile";
-      return false;
+  // stages: about 192 KB of shared memory per CTA, one CTA per SM
+  if (!split) {
+    switch (BN) {
+      case 64: return launch<64, 8, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 128: return launch<128, 6, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 256: return launch<256, 4, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+    }
+  } else {
+    switch (BN) {
+      case 64: return launch<64, 4, true>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 128: return launch<128, 3, true>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 256: return launch<256, 2, true>(ta, tb, ta_lo, tb_lo, p, st, err);
+    }
   }
+  *err = "unsupported N tile";
+  return false;
 }
 
 }  // namespace idf

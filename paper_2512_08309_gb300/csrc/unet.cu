@@ -445,6 +445,124 @@ __global__ void __launch_bounds__(256) conv_out_kernel(const TA* __restrict__ x,
   }
 }
 
+// Row-tiled thin convolutions: CTA (row block, window) stages R rows of its
+// window plus a one-pixel halo in shared memory (zero outside the window)
+// and keeps all index arithmetic in 32 bits.
+constexpr int THIN_R = 8;
+
+// In-conv C_in (1 or 2) -> C_out: thread = (pixel, 4 output channels).
+template <int CIN>
+__global__ void __launch_bounds__(256) conv_in_tile_kernel(const float* __restrict__ x,
+                                                           const float* __restrict__ wk,
+                                                           float* __restrict__ y, int H, int W,
+                                                           int Cout) {
+  extern __shared__ float sm[];
+  const int R = THIN_R;
+  float* xs = sm;                                   // [R+2][W+2][CIN]
+  float* ws = sm + (R + 2) * (W + 2) * CIN;         // [9*CIN][Cout]
+  const int r0 = blockIdx.x * R;
+  const int64_t b = blockIdx.y;
+  const float* xb = x + b * H * W * CIN;
+  for (int i = threadIdx.x; i < (R + 2) * (W + 2) * CIN; i += blockDim.x) {
+    const int c = i % CIN, pc = (i / CIN) % (W + 2), pr = i / (CIN * (W + 2));
+    const int gy = r0 + pr - 1, gx = pc - 1;
+    xs[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? xb[(gy * W + gx) * CIN + c] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < 9 * CIN * Cout; i += blockDim.x) ws[i] = wk[i];
+  __syncthreads();
+  const int Q = Cout / 4;
+  const int P = blockDim.x / Q;
+  const int q = threadIdx.x % Q;
+  if (threadIdx.x / Q >= P) return;
+  float* yb = y + (b * H + r0) * W * Cout;
+  for (int pix = threadIdx.x / Q; pix < R * W; pix += P) {
+    const int pr = pix / W, pc = pix % W;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+      for (int c = 0; c < CIN; ++c) {
+        const float xv = xs[((pr + tap / 3) * (W + 2) + pc + tap % 3) * CIN + c];
+        const float4 w4 = reinterpret_cast<const float4*>(ws + (tap * CIN + c) * Cout)[q];
+        acc.x = fmaf(xv, w4.x, acc.x);
+        acc.y = fmaf(xv, w4.y, acc.y);
+        acc.z = fmaf(xv, w4.z, acc.z);
+        acc.w = fmaf(xv, w4.w, acc.w);
+      }
+    }
+    reinterpret_cast<float4*>(yb + pix * Cout)[q] = acc;
+  }
+}
+
+// Out-conv C_in -> 1: thread = pixels of the row block; input channels are
+// staged 16 at a time, channel-major, so that neighbouring threads read
+// neighbouring columns.
+template <typename TA>
+__global__ void __launch_bounds__(256) conv_out_tile_kernel(const TA* __restrict__ x,
+                                                            const TA* __restrict__ xlo,
+                                                            const float* __restrict__ wk,
+                                                            float* __restrict__ y, int H, int W,
+                                                            int Cin) {
+  extern __shared__ float sm[];
+  const int R = THIN_R, CH = 16;
+  const int RW = (R + 2) * (W + 2);
+  float* xs = sm;               // [CH][R+2][W+2]
+  float* ws = sm + CH * RW;     // [9][Cin]
+  const int r0 = blockIdx.x * R;
+  const int64_t b = blockIdx.y;
+  const TA* xb = x + b * H * W * Cin;
+  const TA* xlb = xlo ? xlo + b * H * W * Cin : nullptr;
+  for (int i = threadIdx.x; i < 9 * Cin; i += blockDim.x) ws[i] = wk[i];
+  float acc[(THIN_R * 128 + 255) / 256];
+  const int npix = R * W;
+  const int per = (npix + blockDim.x - 1) / blockDim.x;
+  for (int j = 0; j < per; ++j) acc[j] = 0.0f;
+  for (int c0 = 0; c0 < Cin; c0 += CH) {
+    __syncthreads();
+    // halo pixel p, 8 channels per thread
+    for (int i = threadIdx.x; i < RW * 2; i += blockDim.x) {
+      const int p = i / 2, h8 = (i % 2) * 8;
+      const int pr = p / (W + 2), pc = p % (W + 2);
+      const int gy = r0 + pr - 1, gx = pc - 1;
+      float v[8];
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        const int64_t off = ((int64_t)gy * W + gx) * Cin + c0 + h8;
+        Load8<TA>::load(xb + off, v);
+        if (xlb) {
+          float vl[8];
+          Load8<TA>::load(xlb + off, vl);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] += vl[k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) xs[(h8 + k) * RW + p] = v[k];
+    }
+    __syncthreads();
+    for (int j = 0; j < per; ++j) {
+      const int pix = threadIdx.x + j * blockDim.x;
+      if (pix >= npix) break;
+      const int pr = pix / W, pc = pix % W;
+      float a = acc[j];
+      for (int ch = 0; ch < CH; ++ch) {
+        const float* xc = xs + ch * RW + pr * (W + 2) + pc;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap)
+          a = fmaf(xc[(tap / 3) * (W + 2) + tap % 3], ws[tap * Cin + c0 + ch], a);
+      }
+      acc[j] = a;
+    }
+  }
+  float* yb = y + (b * H + r0) * W;
+  for (int j = 0; j < per; ++j) {
+    const int pix = threadIdx.x + j * blockDim.x;
+    if (pix < npix) yb[pix] = acc[j];
+  }
+}
+
 // Attention with a compile-time head width: query and output rows stay in
 // registers; keys and values of the head are staged in shared memory.
 template <typename T, int D>
@@ -839,6 +957,27 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
   }
   const int64_t M = (int64_t)c.n * H * W;
   const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, flops, 0.0) : -1;
+  if (w.ks == 3 && x_f32 && !res && w.cin <= 2 && w.cout % 4 == 0 && w.cout <= 1024 && H % THIN_R == 0 &&
+      W <= 128) {
+    const size_t smem = ((size_t)(THIN_R + 2) * (W + 2) * w.cin + 9 * w.cin * w.cout) * sizeof(float);
+    const dim3 grid(H / THIN_R, c.n);
+    cudaFuncSetAttribute(conv_in_tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(conv_in_tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (w.cin == 1) conv_in_tile_kernel<1><<<grid, 256, smem, c.st>>>((const float*)x, w.w32, y, H, W, w.cout);
+    else conv_in_tile_kernel<2><<<grid, 256, smem, c.st>>>((const float*)x, w.w32, y, H, W, w.cout);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches++;
+    return;
+  }
+  if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 16 == 0 && H % THIN_R == 0 && W <= 128) {
+    const size_t smem = ((size_t)16 * (THIN_R + 2) * (W + 2) + 9 * w.cin) * sizeof(float);
+    const dim3 grid(H / THIN_R, c.n);
+    cudaFuncSetAttribute(conv_out_tile_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    conv_out_tile_kernel<TA><<<grid, 256, smem, c.st>>>((const TA*)x, (const TA*)x_lo, w.w32, y, H, W, w.cin);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches++;
+    return;
+  }
   if (w.ks == 3 && x_f32 && !res && w.cin <= 2 && w.cout % 4 == 0) {
     const int64_t tot = M * (w.cout / 4);
     if (w.cin == 1) conv_in_kernel<1><<<grid1d(tot, 256), 256, 0, c.st>>>((const float*)x, w.w32, y, c.n, H, W, w.cout);
