@@ -676,6 +676,50 @@ __global__ void upcat_kernel(const T* __restrict__ a, int Ca, const T* __restric
   }
 }
 
+// Vectorised resampling for channel counts that are multiples of 4: one
+// float4 per thread, index arithmetic in 32 bits within a window.
+__global__ void avgpool2_v4_kernel(const float* __restrict__ x, int n, int H, int W, int C,
+                                   float* __restrict__ y) {
+  const int Ho = H / 2, Wo = W / 2, C4 = C / 4;
+  const int per = Ho * Wo * C4;
+  const int64_t total = (int64_t)n * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / per);
+    const int r = (int)(i - (int64_t)b * per);
+    const int c4 = r % C4, pix = r / C4;
+    const int xo = pix % Wo, yo = pix / Wo;
+    const float4* p = reinterpret_cast<const float4*>(x + (int64_t)b * H * W * C) +
+                      ((2 * yo) * W + 2 * xo) * C4 + c4;
+    const float4 a = p[0], bb = p[C4], c = p[W * C4], d = p[W * C4 + C4];
+    reinterpret_cast<float4*>(y)[i] =
+        make_float4(0.25f * ((a.x + bb.x) + (c.x + d.x)), 0.25f * ((a.y + bb.y) + (c.y + d.y)),
+                    0.25f * ((a.z + bb.z) + (c.z + d.z)), 0.25f * ((a.w + bb.w) + (c.w + d.w)));
+  }
+}
+
+__global__ void upcat_v4_kernel(const float* __restrict__ a, int Ca, const float* __restrict__ sk,
+                                int Cb, int n, int H, int W, float* __restrict__ y) {
+  const int C4 = (Ca + Cb) / 4, Ca4 = Ca / 4, Cb4 = Cb / 4;
+  const int per = H * W * C4;
+  const int64_t total = (int64_t)n * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / per);
+    const int r = (int)(i - (int64_t)b * per);
+    const int c4 = r % C4, pix = r / C4;
+    float4 v;
+    if (c4 < Ca4) {
+      const int xx = pix % W, yy = pix / W;
+      v = reinterpret_cast<const float4*>(a + (int64_t)b * (H / 2) * (W / 2) * Ca)
+          [((yy / 2) * (W / 2) + xx / 2) * Ca4 + c4];
+    } else {
+      v = reinterpret_cast<const float4*>(sk + (int64_t)b * H * W * Cb)[pix * Cb4 + (c4 - Ca4)];
+    }
+    reinterpret_cast<float4*>(y)[i] = v;
+  }
+}
+
 // ------------------------------------------------------------ attention
 // One CTA per (window, head); thread t owns query token t; keys and values
 // of the head are staged in shared memory as float32; online softmax.
@@ -1083,7 +1127,12 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     prev = d.ch[l];
     if (l < L - 1) {
       const int64_t tot = (int64_t)n * (b.H / 2) * (b.H / 2) * prev;
-      avgpool2_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>((const float*)b.SK, n, b.H, b.H, prev, (float*)u->lv[l + 1].P);
+      const int pr = u->prof ? u->prof->begin(PK_RESAMPLE, st, 0.0, 5.0 * tot) : -1;
+      if (prev % 4 == 0)
+        avgpool2_v4_kernel<<<grid1d(tot / 4, 256), 256, 0, st>>>((const float*)b.SK, n, b.H, b.H, prev, (float*)u->lv[l + 1].P);
+      else
+        avgpool2_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>((const float*)b.SK, n, b.H, b.H, prev, (float*)u->lv[l + 1].P);
+      if (u->prof) u->prof->end(pr, st);
       u->launches++;
     }
   }
@@ -1116,7 +1165,12 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   for (int l = L - 2; l >= 0; --l) {
     LevelBufs& b = u->lv[l];
     const int64_t tot = (int64_t)n * b.H * b.H * (prev + d.ch[l]);
-    upcat_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>((const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], n, b.H, b.H, (float*)b.CAT);
+    const int pr = u->prof ? u->prof->begin(PK_RESAMPLE, st, 0.0, 8.0 * tot) : -1;
+    if (prev % 4 == 0 && d.ch[l] % 4 == 0)
+      upcat_v4_kernel<<<grid1d(tot / 4, 256), 256, 0, st>>>((const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], n, b.H, b.H, (float*)b.CAT);
+    else
+      upcat_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>((const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], n, b.H, b.H, (float*)b.CAT);
+    if (u->prof) u->prof->end(pr, st);
     u->launches++;
     resblock<TA>(c, wi, b, (const float*)b.CAT, prev + d.ch[l], d.ch[l], (float*)b.M);
     prev = d.ch[l];

@@ -159,3 +159,25 @@ def test_division_by_zero_is_zero():
     world = S.World(0, synth.stack([lv]), None)
     out = world.model(0, 0, 1, 12)[0]
     assert np.all(out[4:6] == 0.0) and np.all(out[0:4] != 0.0)
+
+
+def test_conditioning_closed_form_two_level():
+    # Identity denoisers (F = sum of input channels) on a two-level stack: the
+    # coarse level follows the one-channel closed form, and every fine pixel
+    # (x, y) follows J <- c_skip J + c_out (c_in J + L(floor(x/8), floor(y/8)))
+    # + sigma N with L the coarse result, unscaled (Sec. 5.3 conditioning by
+    # nearest-neighbour upsampling).
+    st = synth.small_hier_stack(steps=3, window=16, stride=8, test_denoiser=2)
+    world = S.World(4, st, None)
+    y0, x0, h, w = -13, 21, 11, 19
+    got = world.model(y0, x0, h, w)
+    coarse_lv, fine_lv = st["level"]
+    cy0, cx0 = y0 // 8, x0 // 8
+    cy1, cx1 = (y0 + h - 1) // 8, (x0 + w - 1) // 8
+    Lc = _closed_form_pixelwise(coarse_lv, 4, 0, cy0, cx0, cy1 - cy0 + 1, cx1 - cx0 + 1,
+                                lambda J, ci, k: ci * J)
+    ys = np.arange(y0, y0 + h) // 8 - cy0
+    xs = np.arange(x0, x0 + w) // 8 - cx0
+    cond = Lc[np.ix_(ys, xs)]
+    ref = _closed_form_pixelwise(fine_lv, 4, 1, y0, x0, h, w, lambda J, ci, k: ci * J + cond)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
