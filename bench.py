@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "fp32"])
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
+    p.add_argument("--student", type=int, default=0,
+                   help="distillation mode: train the student on N pairs from the plain sampler, judge it")
+    p.add_argument("--epochs", type=int, default=4)
+    p.add_argument("--student-query", type=int, default=2048)
     p.add_argument("--profile-unet", type=int, default=0,
                    help="profiling mode: one warm-up and one timed fine-level UNet forward on N windows")
     p.add_argument("--no-e2e", action="store_true")
@@ -451,8 +455,142 @@ def run_profile_unet(args):
     return 0
 
 
+def run_student(args):
+    """Distil the half-width 2-step student from the plain sampler.
+
+    Pairs: 128x128 crops of the plain 16-channel sampler's output (targets) and
+    that sampler's own initial noise sigma_0 N(seed, 0, 0, .) over the crop
+    (inputs).  Loss: D(x; 80) vs t on the noise, plus D(t + 0.35 N(seed, 0, 1, .);
+    0.35) vs t.  AdamW lr 2e-4, batch 64.  Then the trained student runs as a
+    2-step InfiniteDiffusion level (128 windows, stride 64) and is judged
+    window by window against the plain sampler over the same regions."""
+    import numpy as np
+    import torch
+
+    import paper_2512_08309_gb300 as idf
+    import synth
+    dev = torch.device("cuda", 0)
+    n_pairs, H = args.student, 128
+    c1 = synth.config1_stack()
+    c1w = [synth.weights(idf.param_shapes(lv), 0, i) for i, lv in enumerate(c1["level"])]
+    plain = idf.World(0, c1, c1w, precision="fp32")
+    # targets: crops of 1024 x 1024 plain queries at far-apart locations
+    side, per = 1024, (1024 // H) ** 2
+    n_q = (n_pairs + per - 1) // per
+    t_gen = time.perf_counter()
+    T = torch.empty((n_q * per, H, H), device=dev)
+    N0 = torch.empty_like(T)
+    N1 = torch.empty_like(T)
+    big = torch.empty((side, side), device=dev)
+    for q in range(n_q):
+        x0, y0 = (q * 7 + 1) * (1 << 20), (q * 13 + 5) * (1 << 19)
+        plain.query_device(x0, y0, side, side, big.data_ptr(), side)
+        torch.cuda.synchronize()
+        for a in range(side // H):
+            for b in range(side // H):
+                i = q * per + a * (side // H) + b
+                T[i] = big[a * H:(a + 1) * H, b * H:(b + 1) * H]
+                idf.noise_fill(0, 0, 0, x0 + b * H, y0 + a * H, H, H, N0[i].data_ptr(), H)
+                idf.noise_fill(0, 0, 1, x0 + b * H, y0 + a * H, H, H, N1[i].data_ptr(), H)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    T, N0, N1 = T[:n_pairs], N0[:n_pairs], N1[:n_pairs]
+    n_hold = max(64, n_pairs // 16)
+    n_train = n_pairs - n_hold
+    lv = synth.student_level()
+    w0 = synth.weights(idf.param_shapes(lv), 0, 0)
+    bs = 64
+    S = idf.Student(lv, w0, max_batch=bs)
+
+    def held_out_loss():
+        tot, cnt = 0.0, 0
+        for i in range(n_train, n_pairs, bs):
+            j = min(n_pairs, i + bs)
+            x = (80.0 * N0[i:j]).contiguous()
+            tot += S.loss_grad(x.data_ptr(), T[i:j].contiguous().data_ptr(), j - i, 80.0) * (j - i)
+            cnt += j - i
+        S.zero_grad()
+        return tot / cnt
+
+    loss_before = held_out_loss()
+    g = torch.Generator(device="cpu").manual_seed(0)
+    t_train = time.perf_counter()
+    steps = 0
+    curve = []
+    for ep in range(args.epochs):
+        perm = torch.randperm(n_train, generator=g).to(dev)
+        ep_loss = 0.0
+        for i in range(0, n_train - bs + 1, bs):
+            idx = perm[i:i + bs]
+            t = T[idx].contiguous()
+            x80 = (80.0 * N0[idx]).contiguous()
+            xm = (t + 0.35 * N1[idx]).contiguous()
+            l1 = S.loss_grad(x80.data_ptr(), t.data_ptr(), bs, 80.0)
+            l2 = S.loss_grad(xm.data_ptr(), t.data_ptr(), bs, 0.35)
+            S.adamw(lr=2e-4, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01)
+            ep_loss += l1 + l2
+            steps += 1
+        curve.append(ep_loss / max(1, (n_train // bs)))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    loss_after = held_out_loss()
+    w_trained = S.weights()
+    S.close()
+    # inference: the student as a 2-step InfiniteDiffusion level, judged by the plain sampler
+    st = synth.stack([lv])
+    q = args.student_query
+    res = {}
+    for name, wts in (("student", [w_trained]), ("student_untrained", [w0])):
+        Ws = idf.World(0, st, wts, precision="bf16")
+        out = torch.empty((q, q), device=dev)
+        Ws.query_device(-q // 2, -q // 2, q, q, out.data_ptr(), q)   # warm-up
+        torch.cuda.synchronize()
+        Ws.cache_clear()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Ws.query_device(-q // 2, -q // 2, q, q, out.data_ptr(), q)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        Ws.close()
+        res[name] = (q * q / (ms / 1000.0), out.clone())
+    plain.cache_clear()
+    ref = torch.empty((q, q), device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plain.query_device(-q // 2, -q // 2, q, q, ref.data_ptr(), q)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_pxs = q * q / (e0.elapsed_time(e1) / 1000.0)
+    plain.close()
+    sig = float(ref.std())
+    judged = {}
+    for name in ("student", "student_untrained"):
+        d = (res[name][1] - ref).abs()
+        # judge window by window (128 x 128 at stride 64 covering the query)
+        errs = []
+        for a in range(0, q - H + 1, 64):
+            for b in range(0, q - H + 1, 64):
+                errs.append(float(d[a:a + H, b:b + H].max()) / sig)
+        errs = np.array(errs)
+        judged[name] = {"px_s": res[name][0], "window_err_median": float(np.median(errs)),
+                        "window_err_max": float(errs.max()), "fallback_rate": float((errs > 5e-2).mean()),
+                        "rms_err": float(((res[name][1] - ref) ** 2).mean().sqrt()) / sig}
+    print(json.dumps({
+        "student": {"pairs": n_pairs, "train_pairs": n_train, "held_out": n_hold, "epochs": args.epochs,
+                    "steps": steps, "batch": bs, "pair_gen_s": t_gen, "train_s": t_train,
+                    "train_loss_per_epoch": curve, "held_out_loss_sigma80_before": loss_before,
+                    "held_out_loss_sigma80_after": loss_after,
+                    "gain_held_out_loss": loss_before / loss_after},
+        "inference_query": q, "plain_px_s": plain_pxs, "sigma_out_plain": sig,
+        "judged": judged}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.student:
+        return run_student(args)
     if args.profile_unet:
         return run_profile_unet(args)
     rank, world, local = dist_setup(args.gpus)

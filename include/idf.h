@@ -253,6 +253,49 @@ idf_status idf_laplacian_decode_noalloc(const idf_model_stack* stack, const floa
 idf_status idf_laplacian_halo(const idf_model_stack* stack, int64_t x0, int64_t y0, int32_t w,
                               int32_t h, int64_t L_rect[4], int64_t H_rect[4]);
 
+/* ------------------------------------------------------ learned student */
+
+/* A student denoiser trained on the GPU by this library's own forward and
+ * backward kernels (the build's few-step counterpart of the paper's
+ * consistency-distilled networks, Sec. 5.4 and App. F "Consistency
+ * Distillation").  The network is the UNet of idf_level_desc (same layers and
+ * weight order; no attention block; in_ch = out_ch = 1; `window` is the
+ * training window size); parameters are float32 master weights.  One
+ * training step evaluates D(x; sigma) = c_skip x + c_out S(c_in x) with the
+ * EDM coefficients (sigma_data of the descriptor), the loss mean((D - t)^2),
+ * and adds d loss / d weights to the student's gradient accumulator.
+ * Everything the student holds is owned by the library. */
+typedef struct idf_student idf_student;
+
+/* net->weights (n_weights floats, declaration order) are copied as the
+ * initial weights.  max_batch windows per step; device = CUDA ordinal. */
+idf_status idf_student_create(const idf_level_desc* net, int32_t max_batch, int32_t device,
+                              idf_student** out);
+
+/* x_dev, target_dev: device float32 (n, window, window); 1 <= n <= max_batch.
+ * Writes the batch loss to *loss_out (host) and accumulates its gradient.
+ * Ordered after the caller's stream; synchronizes before returning. */
+idf_status idf_student_loss_grad(idf_student* s, const float* x_dev, const float* target_dev,
+                                 int32_t n, double sigma, double* loss_out, void* cuda_stream);
+
+/* One AdamW step (decoupled weight decay) with the accumulated gradient,
+ * which is then cleared. */
+idf_status idf_student_adamw(idf_student* s, double lr, double beta1, double beta2, double eps,
+                             double weight_decay);
+
+/* Clear the gradient accumulator. */
+idf_status idf_student_zero_grad(idf_student* s);
+
+/* Copy the weights (what = 0) or the accumulated gradient (what = 1) to host
+ * memory in declaration order; n must equal the parameter count. */
+idf_status idf_student_read(const idf_student* s, int32_t what, float* host_out, size_t n);
+
+/* Message of the last failure on this student. */
+const char* idf_student_last_error(const idf_student* s);
+
+/* NULL-safe. */
+void idf_student_destroy(idf_student* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,8 @@ EXPORTS = [
     "idf_world_cache_clear", "idf_world_stats", "idf_world_last_error", "idf_world_destroy",
     "idf_debug_cone", "idf_noise_fill", "idf_model_param_count", "idf_model_param_shape",
     "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo", "idf_laplacian_decode_noalloc",
+    "idf_student_create", "idf_student_loss_grad", "idf_student_adamw", "idf_student_zero_grad",
+    "idf_student_read", "idf_student_last_error", "idf_student_destroy",
 ]
 
 
@@ -107,6 +109,13 @@ def lib():
                                 C.POINTER(i64)], i32),
         "idf_laplacian_decode_noalloc": ([C.POINTER(idf_model_stack), vp, i64, i64, i32, i32, i64, vp, i64,
                                           i64, i32, i32, i64, i64, i64, i32, i32, vp, i64, vp], i32),
+        "idf_student_create": ([C.POINTER(idf_level_desc), i32, i32, C.POINTER(vp)], i32),
+        "idf_student_loss_grad": ([vp, vp, vp, i32, C.c_double, C.POINTER(C.c_double), vp], i32),
+        "idf_student_adamw": ([vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double], i32),
+        "idf_student_zero_grad": ([vp], i32),
+        "idf_student_read": ([vp, i32, C.POINTER(C.c_float), C.c_size_t], i32),
+        "idf_student_last_error": ([vp], C.c_char_p),
+        "idf_student_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -315,3 +324,60 @@ def laplacian_decode_noalloc(stack: dict, L_ptr: int, lrect, lpitch: int, H_ptr:
                                               hrect[3], hpitch, x0, y0, w, h, C.c_void_p(out_ptr), pitch,
                                               _stream_ptr(stream)),
            "idf_laplacian_decode_noalloc")
+
+
+class Student:
+    """idf_student: a student denoiser trained with the library's kernels."""
+
+    def __init__(self, lv: dict, weights, max_batch: int, device: int = 0):
+        import numpy as np
+        self._keep = _Keep()
+        self.lv = lv
+        self.n_params = int(np.asarray(weights).size)
+        d = level_desc(lv, weights, self._keep)
+        h = C.c_void_p()
+        st = lib().idf_student_create(C.byref(d), max_batch, device, C.byref(h))
+        if st != IDF_OK:
+            raise IdfError(st, "idf_student_create")
+        self._h = h
+
+    def _chk(self, st, what):
+        if st != IDF_OK:
+            m = lib().idf_student_last_error(self._h)
+            raise IdfError(st, f"{what}: {m.decode() if m else ''}")
+
+    def loss_grad(self, x_ptr: int, t_ptr: int, n: int, sigma: float, stream=None) -> float:
+        out = C.c_double()
+        self._chk(lib().idf_student_loss_grad(self._h, C.c_void_p(x_ptr), C.c_void_p(t_ptr), n, sigma,
+                                              C.byref(out), _stream_ptr(stream)), "idf_student_loss_grad")
+        return out.value
+
+    def adamw(self, lr=2e-4, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01):
+        self._chk(lib().idf_student_adamw(self._h, lr, beta1, beta2, eps, weight_decay), "idf_student_adamw")
+
+    def zero_grad(self):
+        self._chk(lib().idf_student_zero_grad(self._h), "idf_student_zero_grad")
+
+    def read(self, what: int):
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._chk(lib().idf_student_read(self._h, what, out.ctypes.data_as(C.POINTER(C.c_float)), out.size),
+                  "idf_student_read")
+        return out
+
+    def weights(self):
+        return self.read(0)
+
+    def grads(self):
+        return self.read(1)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().idf_student_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

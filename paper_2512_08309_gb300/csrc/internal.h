@@ -185,4 +185,14 @@ void unet_set_prof(UNet* u, Prof* p);
 // tcgen05 conv availability (compiled in conv_tc.cu)
 bool conv_tc_supported(int cin, int cout, int ks);
 
+// float32 building blocks (unet.cu), NHWC, square images
+void launch_conv_f32(const float* x, const float* wk, const float* res, float* y, int n, int H, int W,
+                     int Cin, int Cout, int ks, cudaStream_t st);
+void launch_gn_f32(const float* x, int n, int H, int C, int G, bool silu, double2* part, float2* stats,
+                   float* y, cudaStream_t st);
+size_t gn_part_elems(int n, int G);
+void launch_avgpool2_f32(const float* x, int n, int H, int C, float* y, cudaStream_t st);
+void launch_upcat_f32(const float* a, int Ca, const float* sk, int Cb, int n, int H, float* y,
+                      cudaStream_t st);
+
 }  // namespace idf

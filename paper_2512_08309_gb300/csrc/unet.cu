@@ -54,11 +54,13 @@ static int grid1d(int64_t n, int block) {
 // Weights wk are float32 [K][Cout].  out = conv(x) (+ res).
 constexpr int CBM = 128, CBN = 64, CBK = 8;
 
+// res may alias y (in-place accumulation: each element is read, then written,
+// by the one thread that owns it).
 template <int KS, typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) conv_simt_kernel(const Tin* __restrict__ x,
                                                         const float* __restrict__ wk,
-                                                        const Tout* __restrict__ res,
-                                                        Tout* __restrict__ y, int n, int H, int W,
+                                                        const Tout* res,
+                                                        Tout* y, int n, int H, int W,
                                                         int Cin, int Cout,
                                                         const Tin* __restrict__ xlo = nullptr) {
   __shared__ float As[CBK][CBM + 4];
@@ -1200,6 +1202,59 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
   if (n <= 0) return true;
   if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err);
   return forward_t<float>(u, x_in, n, F, st, err);
+}
+
+// ------------------------------------------------------------ float32 building blocks
+// (used by the student training engine)
+void launch_conv_f32(const float* x, const float* wk, const float* res, float* y, int n, int H, int W,
+                     int Cin, int Cout, int ks, cudaStream_t st) {
+  const int64_t M = (int64_t)n * H * W;
+  dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((Cout + CBN - 1) / CBN));
+  if (ks == 3) conv_simt_kernel<3, float, float><<<grid, 256, 0, st>>>(x, wk, res, y, n, H, W, Cin, Cout);
+  else conv_simt_kernel<1, float, float><<<grid, 256, 0, st>>>(x, wk, res, y, n, H, W, Cin, Cout);
+}
+
+void launch_gn_f32(const float* x, int n, int H, int C, int G, bool silu, double2* part, float2* stats,
+                   float* y, cudaStream_t st) {
+  const int HW = H * H, Cg = C / G;
+  const int64_t units = (int64_t)n * HW * (C / 8);
+  if (C % 8 == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31)) {
+    const int Q = Cg / 4, P = 256 / Q;
+    int chunk_px = std::max(P, 8192 / Cg);
+    int chunks = (HW + chunk_px - 1) / chunk_px;
+    if (chunks > GN_MAX_CHUNKS) {
+      chunk_px = (HW + GN_MAX_CHUNKS - 1) / GN_MAX_CHUNKS;
+      chunks = (HW + chunk_px - 1) / chunk_px;
+    }
+    gn_partial_kernel<<<dim3(chunks, G, n), 256, 0, st>>>(x, HW, C, G, chunk_px, part);
+    gn_finalize_kernel<<<(n * G + 127) / 128, 128, 0, st>>>(x, part, n, chunks, HW, C, G, stats);
+    const int upw = HW * (C / 8);
+    if (silu)
+      gn_apply8_kernel<float, true><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, y, nullptr, nullptr, nullptr);
+    else
+      gn_apply8_kernel<float, false><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, y, nullptr, nullptr, nullptr);
+    return;
+  }
+  gn_stats_kernel<float><<<n * G, 256, 0, st>>>(x, HW, C, G, stats);
+  const int64_t nel = (int64_t)n * HW * C;
+  if (silu)
+    gn_apply_kernel<float, float, true><<<grid1d(nel, 256), 256, 0, st>>>(x, stats, nel, HW, C, G, y, nullptr, nullptr, nullptr);
+  else
+    gn_apply_kernel<float, float, false><<<grid1d(nel, 256), 256, 0, st>>>(x, stats, nel, HW, C, G, y, nullptr, nullptr, nullptr);
+}
+
+size_t gn_part_elems(int n, int G) { return (size_t)n * G * GN_MAX_CHUNKS; }
+
+void launch_avgpool2_f32(const float* x, int n, int H, int C, float* y, cudaStream_t st) {
+  const int64_t tot = (int64_t)n * (H / 2) * (H / 2) * C;
+  if (C % 4 == 0) avgpool2_v4_kernel<<<grid1d(tot / 4, 256), 256, 0, st>>>(x, n, H, H, C, y);
+  else avgpool2_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>(x, n, H, H, C, y);
+}
+
+void launch_upcat_f32(const float* a, int Ca, const float* sk, int Cb, int n, int H, float* y, cudaStream_t st) {
+  const int64_t tot = (int64_t)n * H * H * (Ca + Cb);
+  if (Ca % 4 == 0 && Cb % 4 == 0) upcat_v4_kernel<<<grid1d(tot / 4, 256), 256, 0, st>>>(a, Ca, sk, Cb, n, H, H, y);
+  else upcat_kernel<float><<<grid1d(tot, 256), 256, 0, st>>>(a, Ca, sk, Cb, n, H, H, y);
 }
 
 }  // namespace idf

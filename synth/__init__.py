@@ -90,6 +90,13 @@ def small_hier_stack(steps: int = 3, window: int = 32, stride: int = 16,
     return stack([coarse, fine], laplacian=1)
 
 
+def student_level(window: int = 128, stride: int = 64) -> dict:
+    """The half-width 2-step student: 4 levels of 32/64/128/128 channels,
+    128x128 windows at stride 64, sigma 80 then 0.35."""
+    return level(levels=4, channels=(32, 64, 128, 128), in_ch=1, out_ch=1, window=window,
+                 stride=stride, steps=2, sigma_max=80.0, sigma_min=0.35)
+
+
 def with_steps(st: dict, steps: int) -> dict:
     st = copy.deepcopy(st)
     for l in st["level"]:
