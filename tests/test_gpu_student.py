@@ -40,7 +40,8 @@ def test_loss_and_gradient_match_oracle(idf, lv, n, sigma):
     w = _w(lv, 1)
     x, t = _batch(n, lv["window"], 2)
     S = idf.Student(lv, w, max_batch=4)
-    loss = S.loss_grad(torch.from_numpy(x).cuda().data_ptr(), torch.from_numpy(t).cuda().data_ptr(), n, sigma)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()   # keep the buffers alive
+    loss = S.loss_grad(xd.data_ptr(), td.data_ptr(), n, sigma)
     g = S.grads().astype(np.float64)
     S.close()
     ref_loss, ref_g = OST.loss_and_grad(lv, w.astype(np.float64), x, t, sigma)
@@ -71,7 +72,8 @@ def test_adamw_step_matches_formula(idf):
     w = _w(lv, 5)
     x, t = _batch(2, 16, 6)
     S = idf.Student(lv, w, max_batch=2)
-    S.loss_grad(torch.from_numpy(x).cuda().data_ptr(), torch.from_numpy(t).cuda().data_ptr(), 2, 1.0)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    S.loss_grad(xd.data_ptr(), td.data_ptr(), 2, 1.0)
     g = S.grads().astype(np.float64)
     S.adamw(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01)
     w1 = S.weights().astype(np.float64)
@@ -94,3 +96,46 @@ def test_training_lowers_the_loss(idf):
     S.close()
     print("loss", losses[0], "->", losses[-1])
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_distillation_gain_over_untrained_student(idf):
+    # Pairs from the plain 16-channel sampler (targets: 128 x 128 crops of its
+    # output; inputs: its own initial noise sigma_0 N(seed, 0, 0, .) there);
+    # training must lower the held-out loss below the untrained student's.
+    c1 = synth.config1_stack()
+    c1w = [synth.weights(idf.param_shapes(lv), 0, i) for i, lv in enumerate(c1["level"])]
+    plain = idf.World(0, c1, c1w, precision="fp32")
+    H, side = 128, 512
+    T, N0 = [], []
+    for q in range(3):
+        x0, y0 = (q * 7 + 1) * (1 << 20), (q * 13 + 5) * (1 << 19)
+        big = plain.query(x0, y0, side, side)
+        for a in range(side // H):
+            for b in range(side // H):
+                T.append(big[a * H:(a + 1) * H, b * H:(b + 1) * H])
+                n0 = torch.empty((H, H), device="cuda")
+                idf.noise_fill(0, 0, 0, x0 + b * H, y0 + a * H, H, H, n0.data_ptr(), H)
+                N0.append(n0)
+    plain.close()
+    T = torch.from_numpy(np.stack(T)).cuda()
+    X = 80.0 * torch.stack(N0)
+    tr, ho = slice(0, 40), slice(40, 48)
+    lv = synth.student_level()
+    S = idf.Student(lv, synth.weights(idf.param_shapes(lv), 0, 0), max_batch=8)
+
+    def held_out():
+        x, t = X[ho].contiguous(), T[ho].contiguous()
+        v = S.loss_grad(x.data_ptr(), t.data_ptr(), 8, 80.0)
+        S.zero_grad()
+        return v
+
+    before = held_out()
+    for it in range(25):
+        i = (it * 8) % 40
+        x, t = X[i:i + 8].contiguous(), T[i:i + 8].contiguous()
+        S.loss_grad(x.data_ptr(), t.data_ptr(), 8, 80.0)
+        S.adamw(lr=1e-3)
+    after = held_out()
+    S.close()
+    print(f"held-out loss {before:.4e} -> {after:.4e}")
+    assert after < 0.9 * before
