@@ -49,6 +49,9 @@ def parse():
                    help="distillation mode: train the student on N pairs from the plain sampler, judge it")
     p.add_argument("--epochs", type=int, default=4)
     p.add_argument("--student-query", type=int, default=2048)
+    p.add_argument("--serve", type=int, default=0,
+                   help="serving mode: N random-access queries on the plain 16-channel stack, batched vs one by one")
+    p.add_argument("--in-flight", type=int, default=64)
     p.add_argument("--profile-unet", type=int, default=0,
                    help="profiling mode: one warm-up and one timed fine-level UNet forward on N windows")
     p.add_argument("--no-e2e", action="store_true")
@@ -587,8 +590,69 @@ def run_student(args):
     return 0
 
 
+def run_serve(args):
+    """Batched lazy random access: the seeded query workload (sides log-uniform
+    in [64, 2048], centres uniform in +-1e6, 30% overlapping an earlier query)
+    on the plain 16-channel stack, served closed-loop in groups of at most
+    `in_flight` queries through idf_world_query_batch (all windows of a step
+    across the group share launches), and the same queries one by one."""
+    import numpy as np
+    import torch
+
+    import paper_2512_08309_gb300 as idf
+    import synth
+    dev = torch.device("cuda", 0)
+    qs = synth.random_queries(args.serve, seed=0)
+    st = synth.config1_stack()
+    wts = [synth.weights(idf.param_shapes(lv), 0, i) for i, lv in enumerate(st["level"])]
+    maxpx = max(w * h for _, _, w, h in qs)
+    bufs = [torch.empty(maxpx, device=dev) for _ in range(args.in_flight)]
+    out = {}
+    for mode in ("batched", "single"):
+        W = idf.World(0, st, wts, precision=args.precision if args.precision != "bf16x3" else "fp32")
+        # warm-up on an unrelated region
+        W.query_device(5 << 30, 5 << 30, 256, 256, bufs[0].data_ptr(), 256)
+        torch.cuda.synchronize()
+        W.cache_clear()
+        s0 = W.stats()
+        lat = []
+        t_all = time.perf_counter()
+        if mode == "batched":
+            for g0 in range(0, len(qs), args.in_flight):
+                grp = qs[g0:g0 + args.in_flight]
+                t0 = time.perf_counter()
+                W.query_batch([(x0, y0, w, h, bufs[i].data_ptr(), w) for i, (x0, y0, w, h) in enumerate(grp)])
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                lat += [dt] * len(grp)
+        else:
+            for (x0, y0, w, h) in qs:
+                t0 = time.perf_counter()
+                W.query_device(x0, y0, w, h, bufs[0].data_ptr(), w)
+                torch.cuda.synchronize()
+                lat.append(time.perf_counter() - t0)
+        total = time.perf_counter() - t_all
+        s1 = W.stats()
+        W.close()
+        px = sum(w * h for _, _, w, h in qs)
+        l0, l1 = s0["levels"][0], s1["levels"][0]
+        hits, miss = l1["cache_hits"] - l0["cache_hits"], l1["cache_misses"] - l0["cache_misses"]
+        out[mode] = {"px_s": px / total, "total_s": total, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                     "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                     "windows": l1["windows_evaluated"] - l0["windows_evaluated"],
+                     "cache_hit_rate": hits / max(1, hits + miss),
+                     "launches": s1["kernel_launches"] - s0["kernel_launches"]}
+    print(json.dumps({"serve": {"queries": len(qs), "px": sum(w * h for _, _, w, h in qs), "in_flight": args.in_flight,
+                                "stack": "plain 16-channel UNet, 32x32 windows at stride 16, 4 steps",
+                                "precision": "fp32", "latency": "per query: submission of its group to completion",
+                                **out}}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.serve:
+        return run_serve(args)
     if args.student:
         return run_student(args)
     if args.profile_unet:
