@@ -351,6 +351,122 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
   }
 }
 
+// GroupNorm of a virtual channel concat [nearest-up2(a) (Ca channels), b (Cb
+// channels)] at resolution H, without materialising it: the same passes as
+// above, each float4 / 8-channel unit reading from the source that holds its
+// channels (Ca % 8 == 0, so no unit straddles the two).
+struct CatSrc {
+  const float* a;   // (n, H/2, H/2, Ca)
+  const float* b;   // (n, H, H, Cb)
+  int Ca, Cb, H;
+};
+
+__device__ __forceinline__ const float* cat_ptr(const CatSrc& s, int64_t win, int p, int c) {
+  if (c < s.Ca) {
+    const int y = p / s.H, x = p % s.H, h2 = s.H / 2;
+    return s.a + ((win * h2 + y / 2) * h2 + x / 2) * s.Ca + c;
+  }
+  return s.b + (win * s.H * s.H + p) * s.Cb + (c - s.Ca);
+}
+
+__global__ void __launch_bounds__(256) gn_partial_cat_kernel(CatSrc src, int G, int chunk_px,
+                                                             double2* __restrict__ part) {
+  __shared__ float r1[8], r2[8];
+  const int C = src.Ca + src.Cb, HW = src.H * src.H;
+  const int Cg = C / G;
+  const int Q = Cg / 4;
+  const int P = blockDim.x / Q;
+  const int t = threadIdx.x;
+  const int q = t % Q, pl = t / Q;
+  const int chunk = blockIdx.x, g = blockIdx.y, b = blockIdx.z;
+  const int p0 = chunk * chunk_px;
+  const int p1 = min(HW, p0 + chunk_px);
+  const float k = *cat_ptr(src, b, 0, g * Cg);
+  float s1 = 0.0f, s2 = 0.0f;
+  if (pl < P) {
+    for (int p = p0 + pl; p < p1; p += P) {
+      const float4 v = *reinterpret_cast<const float4*>(cat_ptr(src, b, p, g * Cg + 4 * q));
+      const float a = v.x - k, bb = v.y - k, c = v.z - k, d = v.w - k;
+      s1 += (a + bb) + (c + d);
+      s2 += (a * a + bb * bb) + (c * c + d * d);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if ((t & 31) == 0) {
+    r1[t >> 5] = s1;
+    r2[t >> 5] = s2;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += (double)r1[w];
+      c += (double)r2[w];
+    }
+    part[((int64_t)b * G + g) * gridDim.x + chunk] = make_double2(a, c);
+  }
+}
+
+__global__ void gn_finalize_cat_kernel(CatSrc src, const double2* __restrict__ part, int n_win, int chunks,
+                                       int G, float2* __restrict__ stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_win * G) return;
+  const int b = i / G, g = i % G;
+  const int C = src.Ca + src.Cb, Cg = C / G, HW = src.H * src.H;
+  double s1 = 0.0, s2 = 0.0;
+  for (int c = 0; c < chunks; ++c) {
+    const double2 pp = part[(int64_t)i * chunks + c];
+    s1 += pp.x;
+    s2 += pp.y;
+  }
+  const double n = (double)HW * Cg;
+  const double k = (double)*cat_ptr(src, b, 0, g * Cg);
+  const double m1 = s1 / n;
+  const double var = fmax(0.0, s2 / n - m1 * m1);
+  stats[i] = make_float2((float)(k + m1), (float)(1.0 / sqrt(var + 1e-5)));
+}
+
+template <typename TA, bool SILU>
+__global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const float2* __restrict__ stats,
+                                                            int n_units, int G, TA* __restrict__ y,
+                                                            TA* __restrict__ copy, TA* __restrict__ ylo,
+                                                            TA* __restrict__ copylo) {
+  const int C = src.Ca + src.Cb, C8 = C / 8, Cg = C / G, HW = src.H * src.H;
+  const int upw = HW * C8;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+    const int b = u / upw;
+    const int r = u - b * upw;
+    const int p = r / C8, c0 = (r % C8) * 8;
+    const float2 ms = stats[b * G + c0 / Cg];
+    const float4* srcp = reinterpret_cast<const float4*>(cat_ptr(src, b, p, c0));
+    const float4 a = srcp[0], bq = srcp[1];
+    float xv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float z = (xv[j] - ms.x) * ms.y;
+      if (SILU) z = z / (1.0f + expf(-z));
+      v[j] = z;
+    }
+    Pack8<TA>::store(y + (int64_t)u * 8, v);
+    if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+    if (ylo) {
+      float rr[8], rc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        rr[j] = v[j] - ld<TA>(y + (int64_t)u * 8 + j);
+        rc[j] = copy ? xv[j] - ld<TA>(copy + (int64_t)u * 8 + j) : 0.0f;
+      }
+      Pack8<TA>::store(ylo + (int64_t)u * 8, rr);
+      if (copylo) Pack8<TA>::store(copylo + (int64_t)u * 8, rc);
+    }
+  }
+}
+
 // ------------------------------------------------------------ thin convolutions
 // In-conv (C_in <= 4 -> C_out): thread per (pixel, 4 output channels).
 template <int CIN>
@@ -1093,6 +1209,55 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
   c.u->launches += 2;
 }
 
+// GroupNorm + SiLU of the virtual concat [up2(a), b]; writes the operand y and
+// the copy of the concat (the shortcut's operand), with low parts if split.
+// Returns false when the shape does not fit the fused kernels.
+template <typename TA>
+bool gn_cat(Ctx& c, const float* a, int Ca, const float* b, int Cb, int H, void* y, void* copy, void* ylo,
+            void* copylo) {
+  const int G = c.u->d.groups, C = Ca + Cb, Cg = C / G, HW = H * H;
+  const int64_t units = (int64_t)c.n * HW * (C / 8);
+  if (!(Ca % 8 == 0 && Cb % 8 == 0 && C % G == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31)))
+    return false;
+  if (!c.ok) return true;
+  const double nb = (double)c.n * HW * C;
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (8.0 + sizeof(TA) * 2)) : -1;
+  CatSrc src{a, b, Ca, Cb, H};
+  const int Q = Cg / 4, P = 256 / Q;
+  int chunk_px = std::max(P, 8192 / Cg);
+  int chunks = (HW + chunk_px - 1) / chunk_px;
+  if (chunks > GN_MAX_CHUNKS) {
+    chunk_px = (HW + GN_MAX_CHUNKS - 1) / GN_MAX_CHUNKS;
+    chunks = (HW + chunk_px - 1) / chunk_px;
+  }
+  gn_partial_cat_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(src, G, chunk_px, c.u->gnpart);
+  gn_finalize_cat_kernel<<<(c.n * G + 127) / 128, 128, 0, c.st>>>(src, c.u->gnpart, c.n, chunks, G, c.u->stats);
+  gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
+                                                                       (TA*)copy, (TA*)ylo, (TA*)copylo);
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+  c.u->launches += 3;
+  return true;
+}
+
+// Decoder ResBlock on the virtual concat [up2(a), b] (channels always change,
+// so the residual is the 1x1 shortcut of the concat).
+template <typename TA>
+bool resblock_cat(Ctx& c, size_t& wi, const LevelBufs& lb, const float* a, int Ca, const float* b, int Cb,
+                  int cout, float* Y) {
+  const bool sp = c.u->split;
+  if (Ca + Cb == cout) return false;
+  if (!gn_cat<TA>(c, a, Ca, b, Cb, lb.H, lb.T1, lb.T4, sp ? lb.T1lo : nullptr, sp ? lb.T4lo : nullptr))
+    return false;
+  const ConvW& c1 = c.u->convs[wi++];
+  const ConvW& c2 = c.u->convs[wi++];
+  const ConvW& sk = c.u->convs[wi++];
+  conv_run<TA>(c, c1, lb.T1, false, nullptr, (float*)lb.T2, lb.H, sp ? lb.T1lo : nullptr);
+  conv_run<TA>(c, sk, lb.T4, false, nullptr, (float*)lb.T3, lb.H, sp ? lb.T4lo : nullptr);
+  gn<TA>(c, (const float*)lb.T2, lb.H, cout, lb.T1, true, nullptr, sp ? lb.T1lo : nullptr);
+  conv_run<TA>(c, c2, lb.T1, false, (const float*)lb.T3, Y, lb.H, sp ? lb.T1lo : nullptr);
+  return true;
+}
+
 // ResBlock: X (cin, float32) -> Y (cout, float32).
 template <typename TA>
 void resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, int cout, float* Y) {
@@ -1166,6 +1331,11 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   resblock<TA>(c, wi, bl, cur, prev, prev, (float*)bl.M);
   for (int l = L - 2; l >= 0; --l) {
     LevelBufs& b = u->lv[l];
+    if (resblock_cat<TA>(c, wi, b, (const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], d.ch[l],
+                         (float*)b.M)) {
+      prev = d.ch[l];
+      continue;
+    }
     const int64_t tot = (int64_t)n * b.H * b.H * (prev + d.ch[l]);
     const int pr = u->prof ? u->prof->begin(PK_RESAMPLE, st, 0.0, 8.0 * tot) : -1;
     if (prev % 4 == 0 && d.ch[l] % 4 == 0)
