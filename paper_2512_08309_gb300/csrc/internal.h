@@ -170,8 +170,11 @@ struct UNetDesc {
 // Shapes (Cout, Cin, kh, kw) in declaration order.
 std::vector<std::vector<int>> unet_param_shapes(const UNetDesc& d);
 // Create / destroy; weights are host float32 in declaration order.
+// With an arena, the activation buffers are carved from it (levels of a
+// world run one after another and share one arena); otherwise allocated.
 UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max_batch,
-                  Err* err);
+                  Err* err, void* arena = nullptr, size_t arena_bytes = 0);
+size_t unet_arena_bytes(const UNetDesc& d, int precision, int max_batch);
 void unet_destroy(UNet* u);
 int unet_max_batch(const UNet* u);
 size_t unet_bytes_per_window(const UNetDesc& d, int precision);

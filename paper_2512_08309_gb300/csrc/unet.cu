@@ -269,19 +269,35 @@ __global__ void __launch_bounds__(256) gn_partial_kernel(const float* __restrict
   }
 }
 
-__global__ void gn_finalize_kernel(const float* __restrict__ x, const double2* __restrict__ part,
-                                   int n_win, int chunks, int HW, int C, int G,
-                                   float2* __restrict__ stats) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_win * G) return;
-  const int b = i / G, g = i % G;
-  const int Cg = C / G;
-  double s1 = 0.0, s2 = 0.0;
-  for (int c = 0; c < chunks; ++c) {
-    const double2 pp = part[(int64_t)i * chunks + c];
+// Sum of the chunk partials of (window, group) i by one warp: lane l adds
+// chunks l, l+32, ..., then the lanes combine in a fixed butterfly order.
+__device__ __forceinline__ void warp_sum_parts(const double2* __restrict__ part, int64_t i, int chunks,
+                                               double& s1, double& s2) {
+  const int lane = threadIdx.x & 31;
+  s1 = 0.0;
+  s2 = 0.0;
+  for (int c = lane; c < chunks; c += 32) {
+    const double2 pp = part[i * chunks + c];
     s1 += pp.x;
     s2 += pp.y;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+}
+
+__global__ void gn_finalize_kernel(const float* __restrict__ x, const double2* __restrict__ part,
+                                   int n_win, int chunks, int HW, int C, int G,
+                                   float2* __restrict__ stats) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n_win * G) return;
+  const int b = i / G, g = i % G;
+  const int Cg = C / G;
+  double s1, s2;
+  warp_sum_parts(part, i, chunks, s1, s2);
+  if ((threadIdx.x & 31) != 0) return;
   const double n = (double)HW * Cg;
   const double k = (double)x[(int64_t)b * HW * C + g * Cg];
   const double m1 = s1 / n;
@@ -413,16 +429,13 @@ __global__ void __launch_bounds__(256) gn_partial_cat_kernel(CatSrc src, int G, 
 
 __global__ void gn_finalize_cat_kernel(CatSrc src, const double2* __restrict__ part, int n_win, int chunks,
                                        int G, float2* __restrict__ stats) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n_win * G) return;
   const int b = i / G, g = i % G;
   const int C = src.Ca + src.Cb, Cg = C / G, HW = src.H * src.H;
-  double s1 = 0.0, s2 = 0.0;
-  for (int c = 0; c < chunks; ++c) {
-    const double2 pp = part[(int64_t)i * chunks + c];
-    s1 += pp.x;
-    s2 += pp.y;
-  }
+  double s1, s2;
+  warp_sum_parts(part, i, chunks, s1, s2);
+  if ((threadIdx.x & 31) != 0) return;
   const double n = (double)HW * Cg;
   const double k = (double)*cat_ptr(src, b, 0, g * Cg);
   const double m1 = s1 / n;
@@ -681,6 +694,74 @@ __global__ void __launch_bounds__(256) conv_out_tile_kernel(const TA* __restrict
   }
 }
 
+// Register-blocked out-conv: thread = one column x RPT consecutive rows of the
+// row block; per staged channel it keeps the (RPT+2) x 3 neighbourhood in
+// registers, so each weight is loaded once for RPT outputs.
+template <typename TA, int RPT>
+__global__ void __launch_bounds__(256) conv_out_tile2_kernel(const TA* __restrict__ x,
+                                                             const TA* __restrict__ xlo,
+                                                             const float* __restrict__ wk,
+                                                             float* __restrict__ y, int H, int W, int Cin) {
+  extern __shared__ float sm[];
+  const int R = THIN_R, CH = 16;
+  const int W2 = W + 2;
+  const int RW = (R + 2) * W2;
+  float* xs = sm;               // [CH][R+2][W+2]
+  float* ws = sm + CH * RW;     // [9][Cin]
+  const int r0 = blockIdx.x * R;
+  const int64_t b = blockIdx.y;
+  const TA* xb = x + b * H * W * Cin;
+  const TA* xlb = xlo ? xlo + b * H * W * Cin : nullptr;
+  for (int i = threadIdx.x; i < 9 * Cin; i += blockDim.x) ws[i] = wk[i];
+  const int col = threadIdx.x % W, rr = (threadIdx.x / W) * RPT;
+  float acc[RPT];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) acc[j] = 0.0f;
+  for (int c0 = 0; c0 < Cin; c0 += CH) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < RW * 2; i += blockDim.x) {
+      const int p = i / 2, h8 = (i % 2) * 8;
+      const int pr = p / W2, pc = p % W2;
+      const int gy = r0 + pr - 1, gx = pc - 1;
+      float v[8];
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        const int64_t off = ((int64_t)gy * W + gx) * Cin + c0 + h8;
+        Load8<TA>::load(xb + off, v);
+        if (xlb) {
+          float vl[8];
+          Load8<TA>::load(xlb + off, vl);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] += vl[k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) xs[(h8 + k) * RW + p] = v[k];
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int ch = 0; ch < CH; ++ch) {
+      const float* xc = xs + ch * RW + rr * W2 + col;
+      float v[RPT + 2][3];
+#pragma unroll
+      for (int i = 0; i < RPT + 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) v[i][j] = xc[i * W2 + j];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const float wv = ws[tap * Cin + c0 + ch];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) acc[i] = fmaf(v[i + tap / 3][tap % 3], wv, acc[i]);
+      }
+    }
+  }
+  float* yb = y + (b * H + r0) * W;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) yb[(rr + i) * W + col] = acc[i];
+}
+
 // Attention with a compile-time head width: query and output rows stay in
 // registers; keys and values of the head are staged in shared memory.
 template <typename T, int D>
@@ -926,6 +1007,7 @@ struct UNet {
   std::vector<LevelBufs> lv;
   float2* stats = nullptr;
   double2* gnpart = nullptr;  // GroupNorm partials (scratch), max_batch * groups * GN_MAX_CHUNKS
+  bool own_bufs = true;       // false: level buffers are carved from a shared arena
   int* status = nullptr;
   int64_t launches = 0;
   Prof* prof = nullptr;
@@ -998,18 +1080,33 @@ void unet_destroy(UNet* u) {
     cudaFree(c.w16);
     cudaFree(c.w16lo);
   }
-  for (auto& b : u->lv) {
-    cudaFree(b.P); cudaFree(b.SK); cudaFree(b.CAT); cudaFree(b.M);
-    cudaFree(b.T1); cudaFree(b.T2); cudaFree(b.T3); cudaFree(b.T4);
-    cudaFree(b.T1lo); cudaFree(b.T4lo); cudaFree(b.T3lo);
-  }
+  if (u->own_bufs)
+    for (auto& b : u->lv) {
+      cudaFree(b.P); cudaFree(b.SK); cudaFree(b.CAT); cudaFree(b.M);
+      cudaFree(b.T1); cudaFree(b.T2); cudaFree(b.T3); cudaFree(b.T4);
+      cudaFree(b.T1lo); cudaFree(b.T4lo); cudaFree(b.T3lo);
+    }
   cudaFree(u->stats);
   cudaFree(u->gnpart);
   cudaFree(u->status);
   delete u;
 }
 
-UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max_batch, Err* err) {
+// Bytes of the activation buffers for max_batch windows (256-byte aligned each).
+size_t unet_arena_bytes(const UNetDesc& d, int precision, int max_batch) {
+  const bool bfm = precision == 1 || precision == 3;
+  const int nbuf = precision == 3 ? 11 : 8;
+  size_t t = 0;
+  for (int l = 0; l < d.levels; ++l) {
+    const size_t H = (size_t)(d.window >> l);
+    const size_t e = (size_t)max_batch * H * H * level_cmax(d, l);
+    for (int i = 0; i < nbuf; ++i) t += ((e * (i < 6 ? 4 : (bfm ? 2 : 4))) + 255) / 256 * 256;
+  }
+  return t;
+}
+
+UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max_batch, Err* err,
+                  void* arena, size_t arena_bytes) {
   UNet* u = new UNet();
   u->d = d;
   u->precision = precision;
@@ -1057,6 +1154,8 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
     u->convs.push_back(c);
   }
   const size_t B = (size_t)u->max_batch;
+  size_t carve = 0;
+  u->own_bufs = arena == nullptr;
   for (int l = 0; l < d.levels; ++l) {
     LevelBufs b;
     b.H = d.window >> l;
@@ -1066,8 +1165,20 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
     void** ps[11] = {&b.P, &b.SK, &b.CAT, &b.M, &b.T2, &b.T3, &b.T1, &b.T4, &b.T1lo, &b.T4lo, &b.T3lo};
     const int nbuf = u->split ? 11 : 8;
     bool ok = true;
-    for (int i = 0; i < nbuf; ++i)
-      if (ok && !ck(cudaMalloc(ps[i], i < 6 ? bytes : obytes), err, "cudaMalloc UNet workspace")) ok = false;
+    for (int i = 0; i < nbuf; ++i) {
+      const size_t nb = i < 6 ? bytes : obytes;
+      if (arena) {
+        *ps[i] = (char*)arena + carve;
+        carve += (nb + 255) / 256 * 256;
+        if (carve > arena_bytes) {
+          err->code = 2;
+          err->msg = "UNet workspace arena too small";
+          ok = false;
+        }
+      } else if (ok && !ck(cudaMalloc(ps[i], nb), err, "cudaMalloc UNet workspace")) {
+        ok = false;
+      }
+    }
     u->lv.push_back(b);
     if (!ok) { unet_destroy(u); return nullptr; }
   }
@@ -1131,6 +1242,18 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     c.u->launches++;
     return;
   }
+  if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 16 == 0 && H % THIN_R == 0 &&
+      (W == 128 || W == 64 || W == 32)) {
+    const size_t smem = ((size_t)16 * (THIN_R + 2) * (W + 2) + 9 * w.cin) * sizeof(float);
+    const dim3 grid(H / THIN_R, c.n);
+    const int rpt = THIN_R * W / 256;
+    auto kern = rpt == 4 ? conv_out_tile2_kernel<TA, 4> : rpt == 2 ? conv_out_tile2_kernel<TA, 2> : conv_out_tile2_kernel<TA, 1>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, 256, smem, c.st>>>((const TA*)x, (const TA*)x_lo, w.w32, y, H, W, w.cin);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches++;
+    return;
+  }
   if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 16 == 0 && H % THIN_R == 0 && W <= 128) {
     const size_t smem = ((size_t)16 * (THIN_R + 2) * (W + 2) + 9 * w.cin) * sizeof(float);
     const dim3 grid(H / THIN_R, c.n);
@@ -1189,7 +1312,7 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
       chunks = (HW + chunk_px - 1) / chunk_px;
     }
     gn_partial_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(x, HW, C, G, chunk_px, c.u->gnpart);
-    gn_finalize_kernel<<<(c.n * G + 127) / 128, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
+    gn_finalize_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
     const int upw = HW * (C / 8);
     if (silu)
       gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
@@ -1231,7 +1354,7 @@ bool gn_cat(Ctx& c, const float* a, int Ca, const float* b, int Cb, int H, void*
     chunks = (HW + chunk_px - 1) / chunk_px;
   }
   gn_partial_cat_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(src, G, chunk_px, c.u->gnpart);
-  gn_finalize_cat_kernel<<<(c.n * G + 127) / 128, 128, 0, c.st>>>(src, c.u->gnpart, c.n, chunks, G, c.u->stats);
+  gn_finalize_cat_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(src, c.u->gnpart, c.n, chunks, G, c.u->stats);
   gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
                                                                        (TA*)copy, (TA*)ylo, (TA*)copylo);
   if (c.u->prof) c.u->prof->end(pr, c.st);
@@ -1397,7 +1520,7 @@ void launch_gn_f32(const float* x, int n, int H, int C, int G, bool silu, double
       chunks = (HW + chunk_px - 1) / chunk_px;
     }
     gn_partial_kernel<<<dim3(chunks, G, n), 256, 0, st>>>(x, HW, C, G, chunk_px, part);
-    gn_finalize_kernel<<<(n * G + 127) / 128, 128, 0, st>>>(x, part, n, chunks, HW, C, G, stats);
+    gn_finalize_kernel<<<(n * G + 3) / 4, 128, 0, st>>>(x, part, n, chunks, HW, C, G, stats);
     const int upw = HW * (C / 8);
     if (silu)
       gn_apply8_kernel<float, true><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, y, nullptr, nullptr, nullptr);

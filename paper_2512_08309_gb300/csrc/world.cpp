@@ -144,6 +144,7 @@ struct idf_world {
   float* d_taps = nullptr;
   int* d_err = nullptr;
   int32_t* h_tab = nullptr; size_t h_tab_cap = 0; // pinned staging
+  void* arena = nullptr; size_t arena_bytes = 0;  // UNet activations, shared by the levels
   int64_t launches = 0, queries = 0;
   Prof prof;
 };
@@ -815,7 +816,21 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
   if (cudaMalloc(&W->d_err, sizeof(int)) != cudaSuccess || cudaMemset(W->d_err, 0, sizeof(int)) != cudaSuccess)
     return bail(IDF_ECUDA);
   const size_t cache_bytes = opts->cache_bytes ? opts->cache_bytes : ((size_t)8 << 30);
-  const size_t ws_bytes = opts->workspace_bytes ? opts->workspace_bytes : ((size_t)48 << 30);
+  const size_t ws_bytes = opts->workspace_bytes ? opts->workspace_bytes : ((size_t)64 << 30);
+  // one activation arena shared by the levels' UNets (they never run at the
+  // same time): each level batches as many windows as the arena holds
+  size_t arena_need = 0;
+  std::vector<int> batches(stack->n_levels, 0);
+  for (int i = 0; i < stack->n_levels; ++i) {
+    const idf_level_desc& d = stack->level[i];
+    if (d.test_denoiser) continue;
+    UNetDesc ud = unet_desc(d);
+    const size_t per = unet_arena_bytes(ud, opts->precision, 1) + 256 * 11 * d.levels;
+    int mb = opts->max_batch > 0 ? opts->max_batch : (int)std::max<size_t>(1, ws_bytes / per);
+    mb = std::min(mb, 4096);
+    batches[i] = mb;
+    arena_need = std::max(arena_need, unet_arena_bytes(ud, opts->precision, mb));
+  }
   W->prof.on = opts->profile != 0;
   W->lv.resize(stack->n_levels);
   for (int i = 0; i < stack->n_levels; ++i) {
@@ -872,11 +887,12 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
         return bail(IDF_EMODEL);
       }
       UNetDesc ud = unet_desc(L.d);
-      const size_t per = unet_bytes_per_window(ud, opts->precision);
-      int mb = opts->max_batch > 0 ? opts->max_batch : (int)std::max<size_t>(1, ws_bytes / stack->n_levels / per);
-      mb = std::min(mb, 4096);
+      if (!W->arena && arena_need) {
+        if (cudaMalloc(&W->arena, arena_need) != cudaSuccess) return bail(IDF_ENOMEM);
+        W->arena_bytes = arena_need;
+      }
       Err e;
-      L.unet = unet_create(ud, stack->level[i].weights, opts->precision, mb, &e);
+      L.unet = unet_create(ud, stack->level[i].weights, opts->precision, batches[i], &e, W->arena, W->arena_bytes);
       if (!L.unet) {
         return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
       }
@@ -903,7 +919,7 @@ void idf_world_destroy(idf_world* W) {
     cudaFree(L.cache.pool);
   }
   cudaFree(W->F); cudaFree(W->x_in); cudaFree(W->tab); cudaFree(W->dense); cudaFree(W->dec);
-  cudaFree(W->outbuf); cudaFree(W->d_taps); cudaFree(W->d_err);
+  cudaFree(W->outbuf); cudaFree(W->d_taps); cudaFree(W->d_err); cudaFree(W->arena);
   if (W->h_tab) cudaFreeHost(W->h_tab);
   if (W->ev_join) cudaEventDestroy(W->ev_join);
   if (W->st) cudaStreamDestroy(W->st);
