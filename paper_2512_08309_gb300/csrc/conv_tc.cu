@@ -101,6 +101,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
 
 // Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
 // swizzle, 8-row core-matrix groups 1024 bytes apart.
+// The 128-byte swizzle phase follows the shared-memory address bits, so an
+// operand may start 32-byte steps into a row (K steps) or whole 128-byte rows
+// into a staged tile (the horizontal taps of row reuse) with the base-offset
+// field left at zero (measured: setting it to (address >> 7) & 7 applies the
+// phase twice).
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -170,16 +175,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // L2).  The shared-memory ring of STAGES stages runs across tile boundaries;
 // two TMEM accumulators (2 x BN columns) let the epilogue of one tile overlap
 // the main loop of the next.
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, bool DXR>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmA_lo,
                                                          const __grid_constant__ CUtensorMap tmB_lo,
                                                          TcParams p) {
-  constexpr int A_BYTES = BM * 128;
+  // DXR (3x3 convs on 128-pixel rows): a stage holds one kernel row dy: a
+  // 130-pixel activation box (halo columns zero-filled) read by the three
+  // horizontal taps at row offsets 0, 1, 2, and the three taps' weights.
+  constexpr int A_BOX = DXR ? (BM + 2) * 128 : BM * 128;    // bytes TMA writes
+  constexpr int A_BYTES = DXR ? 17 * 1024 : BM * 128;       // region, 1024-aligned
   constexpr int B_BYTES = BN * 128;
-  constexpr int NP = SPLIT ? 2 : 1;                  // hi (and lo) parts per operand
-  constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
+  constexpr int NB = DXR ? 3 : 1;                           // weight tiles per stage
+  constexpr int NP = SPLIT ? 2 : 1;                         // hi (and lo) parts per operand
+  constexpr int STAGE_BYTES = NP * (A_BYTES + NB * B_BYTES);
+  constexpr int TX_BYTES = NP * (A_BOX + NB * B_BYTES);
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -253,16 +264,27 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             ok = false;
             break;
           }
-          const int tap = kk / p.n_kc, kc = kk % p.n_kc;
-          const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
           uint8_t* a = smem + (size_t)s * STAGE_BYTES;
           uint8_t* b = a + NP * A_BYTES;
-          mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-          tma_load_4d(a, &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
-          tma_load_2d(b, &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
-          if (SPLIT) {
-            tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * 64, dx, y0 + dy, win);
-            tma_load_2d(b + B_BYTES, &tmB_lo, &full_bar[s], kc * 64, tap * p.Cout + n0);
+          mbar_expect_tx(&full_bar[s], TX_BYTES);
+          if (DXR) {
+            const int dyi = kk / p.n_kc, kc = kk % p.n_kc;
+            tma_load_4d(a, &tmA, &full_bar[s], kc * 64, -1, y0 + dyi - 1, win);
+            if (SPLIT) tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * 64, -1, y0 + dyi - 1, win);
+            for (int t = 0; t < 3; ++t) {
+              tma_load_2d(b + t * B_BYTES, &tmB, &full_bar[s], kc * 64, (dyi * 3 + t) * p.Cout + n0);
+              if (SPLIT)
+                tma_load_2d(b + (3 + t) * B_BYTES, &tmB_lo, &full_bar[s], kc * 64, (dyi * 3 + t) * p.Cout + n0);
+            }
+          } else {
+            const int tap = kk / p.n_kc, kc = kk % p.n_kc;
+            const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
+            tma_load_4d(a, &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
+            tma_load_2d(b, &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
+            if (SPLIT) {
+              tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * 64, dx, y0 + dy, win);
+              tma_load_2d(b + B_BYTES, &tmB_lo, &full_bar[s], kc * 64, tap * p.Cout + n0);
+            }
           }
           last_issue[s] = (int)it;
         }
@@ -295,11 +317,18 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
           const uint32_t b = a + NP * A_BYTES;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            mma_bf16(d, umma_desc(a + 32 * k), umma_desc(b + 32 * k), idesc, (kk > 0 || k > 0) ? 1u : 0u);
-            if (SPLIT) {
-              mma_bf16(d, umma_desc(a + A_BYTES + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
-              mma_bf16(d, umma_desc(a + 32 * k), umma_desc(b + B_BYTES + 32 * k), idesc, 1u);
+          for (int t = 0; t < NB; ++t) {
+            // DXR: horizontal tap t reads the staged rows starting at row t
+            const uint32_t at = a + (DXR ? 128 * t : 0);
+            const uint32_t bt = b + B_BYTES * t;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              mma_bf16(d, umma_desc(at + 32 * k), umma_desc(bt + 32 * k), idesc,
+                       (kk > 0 || t > 0 || k > 0) ? 1u : 0u);
+              if (SPLIT) {
+                mma_bf16(d, umma_desc(at + A_BYTES + 32 * k), umma_desc(bt + 32 * k), idesc, 1u);
+                mma_bf16(d, umma_desc(at + 32 * k), umma_desc(bt + NB * B_BYTES + 32 * k), idesc, 1u);
+              }
             }
           }
           mma_commit(&empty_bar[s]);
@@ -375,13 +404,13 @@ int sm_count() {
   return n;
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, bool DXR>
 bool launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, const CUtensorMap& blo,
             const TcParams& p, cudaStream_t st, std::string* err) {
-  const size_t smem = (size_t)STAGES * (SPLIT ? 2 : 1) * (BM * 128 + BN * 128) + 1024;
+  const size_t smem = (size_t)STAGES * (SPLIT ? 2 : 1) * ((DXR ? 17 * 1024 : BM * 128) + (DXR ? 3 : 1) * BN * 128) + 1024;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, SPLIT, DXR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
       *err = "cudaFuncSetAttribute failed";
       return false;
@@ -390,7 +419,7 @@ bool launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, 
   }
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sm_count() ? tiles : sm_count();
-  conv_tc_kernel<BN, STAGES, SPLIT><<<grid, 192, smem, st>>>(a, b, alo, blo, p);
+  conv_tc_kernel<BN, STAGES, SPLIT, DXR><<<grid, 192, smem, st>>>(a, b, alo, blo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -425,10 +454,12 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
   const int BN = Cout <= 256 ? Cout : 256;
   const bool split = x_lo && w_lo;
   CUtensorMap ta, tb, ta_lo, tb_lo;
+  // 3x3 convs on 128-pixel rows stage one 130-pixel box per kernel row
+  const bool dxr = ks == 3 && W == 128 && BN == 64;
   auto encA = [&](CUtensorMap* m, const bf16* ptr) {
     cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
     cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)W, (cuuint32_t)(128 / W), 1};
+    cuuint32_t box[4] = {64, (cuuint32_t)(dxr ? W + 2 : W), (cuuint32_t)(dxr ? 1 : 128 / W), 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)ptr, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -447,31 +478,13 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
     *err = "tensor map (low parts) encode failed";
     return false;
   }
-  {
-    cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
-    cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)W, (cuuint32_t)(128 / W), 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)x, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      *err = "tensor map (activations) encode failed";
-      return false;
-    }
+  if (!encA(&ta, x)) {
+    *err = "tensor map (activations) encode failed";
+    return false;
   }
-  {
-    cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)ks * ks * Cout};
-    cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)BN};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)w, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      *err = "tensor map (weights) encode failed";
-      return false;
-    }
+  if (!encB(&tb, w)) {
+    *err = "tensor map (weights) encode failed";
+    return false;
   }
   TcParams p;
   p.res = res;
@@ -482,7 +495,7 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
   p.Cout = Cout;
   p.ks = ks;
   p.n_kc = Cin / 64;
-  p.n_iter = ks * ks * (Cin / 64);
+  p.n_iter = (dxr && BN == 64 ? ks : ks * ks) * (Cin / 64);
   p.m_tiles = (int)((int64_t)n * H * W / BM);
   p.n_tiles = Cout / BN;
   if (!split) {
@@ -490,17 +503,23 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
     tb_lo = tb;
   }
   // stages: about 192 KB of shared memory per CTA, one CTA per SM
+  if (dxr && BN != 64) {
+    *err = "row-reuse staging is built for 64-channel tiles only";
+    return false;
+  }
   if (!split) {
     switch (BN) {
-      case 64: return launch<64, 8, false>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 128: return launch<128, 6, false>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 256: return launch<256, 4, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 64: return dxr ? launch<64, 5, false, true>(ta, tb, ta_lo, tb_lo, p, st, err)
+                          : launch<64, 8, false, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 128: return launch<128, 6, false, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 256: return launch<256, 4, false, false>(ta, tb, ta_lo, tb_lo, p, st, err);
     }
   } else {
     switch (BN) {
-      case 64: return launch<64, 4, true>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 128: return launch<128, 3, true>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 256: return launch<256, 2, true>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 64: return dxr ? launch<64, 2, true, true>(ta, tb, ta_lo, tb_lo, p, st, err)
+                          : launch<64, 4, true, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 128: return launch<128, 3, true, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 256: return launch<256, 2, true, false>(ta, tb, ta_lo, tb_lo, p, st, err);
     }
   }
   *err = "unsupported N tile";
