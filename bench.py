@@ -345,10 +345,17 @@ def run_idf(args, rank, world, local):
     achieved = tc["flops"] / (tc["ms"] / 1000.0) / 1e12 if tc["ms"] > 0 else 0.0
     peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     rec = traffic_record()
+    fpl = tc["flops"] / max(1, tc["launches"])
+    # bf16x3 issues three bf16 products per multiply-add of the convolution
+    mma_factor = 3.0 if args.precision == "bf16x3" else 1.0
     roofline = {"kernel": "conv_tc (tcgen05 implicit-GEMM conv)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_kind": f"{pk_kind} bf16 sustained",
-                "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                "mma_work_factor": mma_factor, "achieved_mma": achieved * mma_factor,
+                "frac_mma": achieved * mma_factor / peak,
+                # DRAM bytes per algorithmic FLOP from the committed ncu capture of the
+                # fine UNet's 23 convolutions, scaled to this run's FLOPs per launch
+                "traffic": rec["dram_bytes_per_algorithmic_flop"] * fpl if rec else None,
                 "algorithmic_bytes_per_launch": tc["bytes"] / max(1, tc["launches"]),
                 "flops_per_launch": tc["flops"] / max(1, tc["launches"]),
                 "avg_launch_ms": tc["ms"] / max(1, tc["launches"]),
