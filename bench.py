@@ -35,6 +35,15 @@ WORKLOAD = ("2-level hierarchy (coarse 64/128/128 @1/8, fine 64/128/256/256 + at
             "128x128 windows stride 64, 20 steps, 4096x4096 metres query, BF16 convs")
 
 
+def bench_config(q: int, precision: str, windows_per_step=None, world: int = 1) -> dict:
+    c = {"workload": WORKLOAD, "query": q, "steps_per_level": 20, "precision": precision,
+         "cache": "emptied every step; working set of several GB per step exceeds L2",
+         "parallelism": f"{world} independent worlds" if world > 1 else "single GPU"}
+    if windows_per_step:
+        c["windows_per_step"] = windows_per_step
+    return c
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -80,12 +89,19 @@ def barrier(world):
         dist.barrier()
 
 
+def query_origin(rank: int, i: int):
+    """Origin of step i's query on a rank: distinct, far-apart 4096^2 regions
+    for every (rank, step), so no rank reuses another's (or its own) tiles."""
+    return (rank * 7919 + i) * (1 << 22) - (1 << 30), ((rank * 104729 + 3 * i) % 1000) * (1 << 21)
+
+
 def max_over_ranks(v, world):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -252,7 +268,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "px/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * QUERY * QUERY / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "query": QUERY},
+        "data": "synthetic", "config": bench_config(QUERY, args.precision),
         "cpu_baseline": {"value": v, "unit": "px/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": elapsed,
@@ -300,8 +316,7 @@ def run_idf(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
 
     def loc(i):
-        # distinct far-apart locations per rank and step; nothing is reused
-        return (rank * 7919 + i) * (1 << 22) - (1 << 30), ((rank * 104729 + 3 * i) % 1000) * (1 << 21)
+        return query_origin(rank, i)
 
     def step(i):
         W.cache_clear()
@@ -372,10 +387,8 @@ def run_idf(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "query": q, "steps_per_level": 20, "precision": args.precision,
-                   "windows_per_step": {"coarse": wins[0] / args.steps, "fine": wins[1] / args.steps},
-                   "cache": "emptied every step; working set of several GB per step exceeds L2",
-                   "parallelism": f"{world} independent worlds" if world > 1 else "single GPU"},
+        "config": bench_config(q, args.precision, {"coarse": wins[0] / args.steps, "fine": wins[1] / args.steps},
+                               world),
         "gpu_launches": launches, "output_finite": finite,
         "roofline": roofline, "hbm_kernels": hbm,
         "kernel_ms": {k: v["ms"] for k, v in prof.items() if v["launches"]},

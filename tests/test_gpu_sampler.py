@@ -217,3 +217,40 @@ def test_laplacian_decode_matches_oracle(idf):
     with pytest.raises(idf.IdfError):
         idf.laplacian_decode(st, Ld.data_ptr(), (Lr[0] + 1, Lr[1], Lr[2] - 1, Lr[3]), Lr[2], Hd.data_ptr(), Hr,
                              Hr[2], x0, y0, w, h, out.data_ptr(), w)
+
+
+# ------------------------------------------------------ degenerate layouts
+
+@pytest.mark.parametrize("window,stride,steps", [
+    (16, 16, 3),   # window = stride: independent tiles (no overlap, Sec. 6 baseline)
+    (48, 16, 2),   # three windows per tile and axis
+    (32, 16, 1),   # a single blended step
+])
+def test_layouts_match_oracle(idf, window, stride, steps):
+    lv = synth.level(window=window, stride=stride, steps=steps, test_denoiser=3)
+    st = synth.stack([lv])
+    W = idf.World(2, st)
+    x0, y0, w, h = -37, 21, 45, 33
+    got = W.query(x0, y0, w, h).astype(np.float64)
+    W.close()
+    ref = OS.World(2, st, None).model(y0, x0, h, w)
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
+def test_extreme_coordinates(idf):
+    st = synth.config1_stack(test_denoiser=2)
+    W = idf.World(0, st)
+    # tile indices near the int32 limit still work and agree with the oracle
+    x0 = (1 << 31) * 16 - 16 * 40
+    got = W.query(x0, -x0, 16, 8).astype(np.float64)
+    ref = OS.World(0, st, None).model(-x0, x0, 8, 16)
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+    # beyond it the request is refused, and the world stays usable
+    with pytest.raises(idf.IdfError) as e:
+        W.query((1 << 40) - 64, 0, 8, 8)
+    assert e.value.status == idf.IDF_EINVAL
+    with pytest.raises(idf.IdfError) as e:
+        W.query_device(0, 0, 1 << 16, (1 << 15) + 1, 0, 1 << 16)
+    assert e.value.status == idf.IDF_EINVAL
+    assert W.query(0, 0, 4, 4).shape == (4, 4)
+    W.close()
