@@ -24,6 +24,13 @@
 //              K step, where x = hi + lo with hi = bf16(x), lo = bf16(x - hi):
 //              bfloat16 products with the rounding of both operands
 //              compensated.
+//   Stats:     optionally the epilogue also emits GroupNorm partials of the
+//              values it writes: per 32-pixel block (one warp's TMEM lanes)
+//              and 16-channel slice, the mean and the sum of squared
+//              deviations M2 of those 512 values (per pixel over 16 channels,
+//              then merged across the warp's lanes by the pairwise update of
+//              Chan et al. 1979).  The GroupNorm then needs no statistics
+//              pass over its input.
 //   Waits:     every mbarrier wait is bounded (clock64 budget); on expiry
 //              the CTA sets the status word, drains what it issued and
 //              frees its TMEM before returning.
@@ -161,6 +168,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 struct TcParams {
   const float* res;
   float* y;
+  float2* bstats;  // null, or (mean, M2) per (32-pixel block, 16-channel slice)
   int* status;
   int H, W, Cout, ks, n_kc, n_iter;
   int m_tiles, n_tiles;  // output tiles: 128-pixel rows x BN channels
@@ -365,6 +373,37 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             v.x += rv.x; v.y += rv.y; v.z += rv.z; v.w += rv.w;
           }
           reinterpret_cast<float4*>(yp)[j] = v;
+          r[4 * j] = __float_as_uint(v.x);
+          r[4 * j + 1] = __float_as_uint(v.y);
+          r[4 * j + 2] = __float_as_uint(v.z);
+          r[4 * j + 3] = __float_as_uint(v.w);
+        }
+        if (p.bstats) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) sum += __uint_as_float(r[16 * h + k]);
+            float mu = sum * 0.0625f, m2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const float dv = __uint_as_float(r[16 * h + k]) - mu;
+              m2 = fmaf(dv, dv, m2);
+            }
+            // merge equal-count partials of lanes l and l ^ o (n values each)
+            float half_n = 16.0f * 0.5f;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const float mo = __shfl_xor_sync(0xffffffffu, mu, o);
+              const float m2o = __shfl_xor_sync(0xffffffffu, m2, o);
+              const float dm = mo - mu;
+              m2 = (m2 + m2o) + dm * dm * half_n;
+              mu = (mu + mo) * 0.5f;
+              half_n *= 2.0f;
+            }
+            if (lane == 0)
+              p.bstats[(m >> 5) * (p.Cout >> 4) + ((n0 + c0) >> 4) + h] = make_float2(mu, m2);
+          }
         }
       }
       fence_before();
@@ -440,8 +479,8 @@ bool conv_tc_shape_ok(int H, int W) {
 }
 
 bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16* w_lo, const float* res,
-                     float* y, int n, int H, int W, int Cin, int Cout, int ks, int* status, cudaStream_t st,
-                     std::string* err) {
+                     float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
+                     cudaStream_t st, std::string* err) {
   if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
     *err = "shape not supported by the tensor-core convolution";
     return false;
@@ -489,6 +528,7 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
   TcParams p;
   p.res = res;
   p.y = y;
+  p.bstats = bstats;
   p.status = status;
   p.H = H;
   p.W = W;

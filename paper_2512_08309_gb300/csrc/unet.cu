@@ -305,6 +305,67 @@ __global__ void gn_finalize_kernel(const float* __restrict__ x, const double2* _
   stats[i] = make_float2((float)(k + m1), (float)(1.0 / sqrt(var + 1e-5)));
 }
 
+// GroupNorm statistics from the partials that the tensor-core convolution's
+// epilogue wrote: (mean, M2) of 512 values per (32-pixel block, 16-channel
+// slice).  One warp per (window, group).  The group's channels may come from
+// two sources, a virtual concat [up2(a), b]; a partial of a counts four times
+// (nearest 2x upsampling repeats each pixel four times: same mean, four times
+// the count and the M2).  Each partial (m_i, M2_i, n_i) becomes shifted sums
+// about k, the mean of the group's first partial: n_i (m_i - k) and
+// M2_i + n_i (m_i - k)^2, added in double per lane in a fixed order and
+// across the lanes in a fixed butterfly, so the result depends neither on
+// the batch nor on the launch.
+struct BlkSrc {
+  const float2* a;   // partials of the upsampled source (null when Ca == 0)
+  const float2* b;
+  int Ca, Cb;        // channels of each source, multiples of 16
+  int bpw_a, bpw_b;  // 32-pixel blocks per window of each source
+};
+
+__global__ void gn_finalize_blk_kernel(BlkSrc src, int n_win, int G, float2* __restrict__ stats) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n_win * G) return;
+  const int lane = threadIdx.x & 31;
+  const int b = i / G, g = i % G;
+  const int Cg = (src.Ca + src.Cb) / G;
+  const int s0 = g * Cg / 16, s1 = (g + 1) * Cg / 16;  // the group's slices of the concat
+  const int sa = src.Ca / 16, sb = src.Cb / 16;
+  const int na = max(0, min(s1, sa) - s0);            // slices from a, starting at s0
+  const int nb = (s1 - s0) - na;                      // slices from b, starting at b0
+  const int b0 = max(s0, sa) - sa;
+  const int Pa = na * src.bpw_a, Pb = nb * src.bpw_b;
+  const double k = na > 0 ? (double)src.a[(int64_t)b * src.bpw_a * sa + s0].x
+                          : (double)src.b[(int64_t)b * src.bpw_b * sb + b0].x;
+  double S1 = 0.0, S2 = 0.0;
+  for (int t = lane; t < Pa + Pb; t += 32) {
+    float2 v;
+    double w, m2;
+    if (t < Pa) {
+      v = src.a[((int64_t)b * src.bpw_a + t / na) * sa + s0 + t % na];
+      w = 2048.0;
+      m2 = 4.0 * (double)v.y;
+    } else {
+      const int u = t - Pa;
+      v = src.b[((int64_t)b * src.bpw_b + u / nb) * sb + b0 + u % nb];
+      w = 512.0;
+      m2 = (double)v.y;
+    }
+    const double d = (double)v.x - k;
+    S1 += w * d;
+    S2 += m2 + w * d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+  }
+  if (lane != 0) return;
+  const double n = 2048.0 * Pa + 512.0 * Pb;
+  const double m1 = S1 / n;
+  const double var = fmax(0.0, S2 / n - m1 * m1);
+  stats[i] = make_float2((float)(k + m1), (float)(1.0 / sqrt(var + 1e-5)));
+}
+
 // y = silu(gn(x)) (or gn(x)) on 8 channels (one group) per thread; copy = x.
 template <typename TA> struct Pack8;
 template <> struct Pack8<float> {
@@ -471,8 +532,8 @@ __global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const fl
       float rr[8], rc[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        rr[j] = v[j] - ld<TA>(y + (int64_t)u * 8 + j);
-        rc[j] = copy ? xv[j] - ld<TA>(copy + (int64_t)u * 8 + j) : 0.0f;
+        rr[j] = v[j] - __bfloat162float(__float2bfloat16_rn(v[j]));
+        rc[j] = xv[j] - __bfloat162float(__float2bfloat16_rn(xv[j]));
       }
       Pack8<TA>::store(ylo + (int64_t)u * 8, rr);
       if (copylo) Pack8<TA>::store(copylo + (int64_t)u * 8, rc);
@@ -788,7 +849,59 @@ __global__ void attention_d_kernel(const float* __restrict__ qkv, int Tn, int C,
       o[c] = 0.0f;
     }
     float mx = -INFINITY, den = 0.0f;
-    for (int j = 0; j < Tn; ++j) {
+    // keys in blocks of KB: KB scores of two independent FMA chains each,
+    // one running-max update per block, then the KB value rows
+    constexpr int KB = 4;
+    int j = 0;
+    for (; j + KB <= Tn; j += KB) {
+      float sc[KB];
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        const float4* kj = reinterpret_cast<const float4*>(Ks + (size_t)(j + u) * D);
+        float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D / 4; c += 2) {
+          const float4 k4 = kj[c], k5 = kj[c + 1];
+          a0 = fmaf(q[4 * c], k4.x, a0);
+          a1 = fmaf(q[4 * c + 4], k5.x, a1);
+          a0 = fmaf(q[4 * c + 1], k4.y, a0);
+          a1 = fmaf(q[4 * c + 5], k5.y, a1);
+          a0 = fmaf(q[4 * c + 2], k4.z, a0);
+          a1 = fmaf(q[4 * c + 6], k5.z, a1);
+          a0 = fmaf(q[4 * c + 3], k4.w, a0);
+          a1 = fmaf(q[4 * c + 7], k5.w, a1);
+        }
+        sc[u] = a0 + a1;
+      }
+      float bm = sc[0];
+#pragma unroll
+      for (int u = 1; u < KB; ++u) bm = fmaxf(bm, sc[u]);
+      if (bm > mx) {
+        const float corr = expf(mx - bm);
+        den *= corr;
+#pragma unroll
+        for (int c = 0; c < D; ++c) o[c] *= corr;
+        mx = bm;
+      }
+      float pj[KB];
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        pj[u] = expf(sc[u] - mx);
+        den += pj[u];
+      }
+#pragma unroll
+      for (int c = 0; c < D / 4; ++c) {
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+          const float4 v4 = reinterpret_cast<const float4*>(Vs + (size_t)(j + u) * D)[c];
+          o[4 * c] = fmaf(pj[u], v4.x, o[4 * c]);
+          o[4 * c + 1] = fmaf(pj[u], v4.y, o[4 * c + 1]);
+          o[4 * c + 2] = fmaf(pj[u], v4.z, o[4 * c + 2]);
+          o[4 * c + 3] = fmaf(pj[u], v4.w, o[4 * c + 3]);
+        }
+      }
+    }
+    for (; j < Tn; ++j) {
       const float4* kj = reinterpret_cast<const float4*>(Ks + (size_t)j * D);
       float sc = 0.0f;
 #pragma unroll
@@ -806,16 +919,16 @@ __global__ void attention_d_kernel(const float* __restrict__ qkv, int Tn, int C,
         for (int c = 0; c < D; ++c) o[c] *= corr;
         mx = sc;
       }
-      const float pj = expf(sc - mx);
-      den += pj;
+      const float p1 = expf(sc - mx);
+      den += p1;
       const float4* vj = reinterpret_cast<const float4*>(Vs + (size_t)j * D);
 #pragma unroll
       for (int c = 0; c < D / 4; ++c) {
         const float4 v4 = vj[c];
-        o[4 * c] = fmaf(pj, v4.x, o[4 * c]);
-        o[4 * c + 1] = fmaf(pj, v4.y, o[4 * c + 1]);
-        o[4 * c + 2] = fmaf(pj, v4.z, o[4 * c + 2]);
-        o[4 * c + 3] = fmaf(pj, v4.w, o[4 * c + 3]);
+        o[4 * c] = fmaf(p1, v4.x, o[4 * c]);
+        o[4 * c + 1] = fmaf(p1, v4.y, o[4 * c + 1]);
+        o[4 * c + 2] = fmaf(p1, v4.z, o[4 * c + 2]);
+        o[4 * c + 3] = fmaf(p1, v4.w, o[4 * c + 3]);
       }
     }
     const float inv = 1.0f / den;
@@ -967,8 +1080,8 @@ __global__ void attention_kernel(const float* __restrict__ qkv, int Tn, int C, i
 
 // ------------------------------------------------------------ engine
 bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16* w_lo, const float* res,
-                     float* y, int n, int H, int W, int Cin, int Cout, int ks, int* status, cudaStream_t st,
-                     std::string* err);
+                     float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
+                     cudaStream_t st, std::string* err);
 bool conv_tc_shape_ok(int H, int W);
 
 struct ConvW {
@@ -996,6 +1109,12 @@ struct LevelBufs {
   void* T1lo = nullptr;  // low parts of T1, T4 and of the attention output (IDF_BF16X3)
   void* T4lo = nullptr;
   void* T3lo = nullptr;
+  // GroupNorm partials written by the tensor-core convolutions into T2, SK,
+  // M and CAT: (mean, M2) per (32-pixel block, 16-channel slice)
+  float2* bT2 = nullptr;
+  float2* bSK = nullptr;
+  float2* bM = nullptr;
+  float2* bCAT = nullptr;
 };
 
 struct UNet {
@@ -1007,6 +1126,7 @@ struct UNet {
   std::vector<LevelBufs> lv;
   float2* stats = nullptr;
   double2* gnpart = nullptr;  // GroupNorm partials (scratch), max_batch * groups * GN_MAX_CHUNKS
+  float2* blkmem = nullptr;   // the levels' block partials (bT2, bSK, bM, bCAT)
   bool own_bufs = true;       // false: level buffers are carved from a shared arena
   int* status = nullptr;
   int64_t launches = 0;
@@ -1088,6 +1208,7 @@ void unet_destroy(UNet* u) {
     }
   cudaFree(u->stats);
   cudaFree(u->gnpart);
+  cudaFree(u->blkmem);
   cudaFree(u->status);
   delete u;
 }
@@ -1182,6 +1303,21 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
     u->lv.push_back(b);
     if (!ok) { unet_destroy(u); return nullptr; }
   }
+  // four block-partial arrays per level, each for max_batch windows of the
+  // level's widest buffer (H^2 / 32 blocks x cmax / 16 slices)
+  size_t nblk = 0;
+  for (auto& b : u->lv) nblk += 4 * (B * b.H * b.H / 32) * ((b.cmax + 15) / 16);
+  if (!ck(cudaMalloc(&u->blkmem, nblk * sizeof(float2)), err, "cudaMalloc GroupNorm block partials")) { unet_destroy(u); return nullptr; }
+  {
+    float2* q = u->blkmem;
+    for (auto& b : u->lv) {
+      const size_t e = (B * b.H * b.H / 32) * ((b.cmax + 15) / 16);
+      b.bT2 = q; q += e;
+      b.bSK = q; q += e;
+      b.bM = q; q += e;
+      b.bCAT = q; q += e;
+    }
+  }
   if (!ck(cudaMalloc(&u->stats, B * d.groups * sizeof(float2)), err, "cudaMalloc stats")) { unet_destroy(u); return nullptr; }
   if (!ck(cudaMalloc(&u->gnpart, B * GN_MAX_CHUNKS * d.groups * sizeof(double2)), err, "cudaMalloc GroupNorm scratch")) { unet_destroy(u); return nullptr; }
   if (!ck(cudaMalloc(&u->status, sizeof(int)), err, "cudaMalloc status") ||
@@ -1204,11 +1340,13 @@ struct Ctx {
   bool ok = true;
 };
 
-// out (float32) = conv(x) (+ res), x in operand type TA (or float32 x_f32)
+// out (float32) = conv(x) (+ res), x in operand type TA (or float32 x_f32).
+// With bs given, the tensor-core path also writes the GroupNorm block
+// partials of out there; returns whether it did.
 template <typename TA>
-void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H,
-              const void* x_lo = nullptr) {
-  if (!c.ok) return;
+bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H,
+              const void* x_lo = nullptr, float2* bs = nullptr) {
+  if (!c.ok) return false;
   const int W = H;
   const double flops = 2.0 * c.n * H * W * (double)w.cout * w.ks * w.ks * w.cin;
   if (std::is_same<TA, bf16>::value && w.tc && !x_f32 && conv_tc_shape_ok(H, W)) {
@@ -1217,8 +1355,8 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     const double by = c.n * H * W * (2.0 * w.cin + 4.0 * w.cout * (res ? 2 : 1)) + 2.0 * w.ks * w.ks * w.cin * w.cout;
     const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
     const bool ok = conv_tc_forward((const bf16*)x, w.w16, c.u->split ? (const bf16*)x_lo : nullptr,
-                                    c.u->split ? w.w16lo : nullptr, res, y, c.n, H, W, w.cin, w.cout, w.ks,
-                         c.u->status, c.st, &e);
+                                    c.u->split ? w.w16lo : nullptr, res, y, bs, c.n, H, W, w.cin, w.cout,
+                                    w.ks, c.u->status, c.st, &e);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     if (!ok) {
       c.ok = false;
@@ -1226,7 +1364,7 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
       c.err->msg = "conv_tc: " + e;
     }
     c.u->launches++;
-    return;
+    return ok && bs != nullptr;
   }
   const int64_t M = (int64_t)c.n * H * W;
   const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, flops, 0.0) : -1;
@@ -1240,7 +1378,7 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     else conv_in_tile_kernel<2><<<grid, 256, smem, c.st>>>((const float*)x, w.w32, y, H, W, w.cout);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
-    return;
+    return false;
   }
   if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 16 == 0 && H % THIN_R == 0 &&
       (W == 128 || W == 64 || W == 32)) {
@@ -1252,7 +1390,7 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     kern<<<grid, 256, smem, c.st>>>((const TA*)x, (const TA*)x_lo, w.w32, y, H, W, w.cin);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
-    return;
+    return false;
   }
   if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 16 == 0 && H % THIN_R == 0 && W <= 128) {
     const size_t smem = ((size_t)16 * (THIN_R + 2) * (W + 2) + 9 * w.cin) * sizeof(float);
@@ -1261,7 +1399,7 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     conv_out_tile_kernel<TA><<<grid, 256, smem, c.st>>>((const TA*)x, (const TA*)x_lo, w.w32, y, H, W, w.cin);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
-    return;
+    return false;
   }
   if (w.ks == 3 && x_f32 && !res && w.cin <= 2 && w.cout % 4 == 0) {
     const int64_t tot = M * (w.cout / 4);
@@ -1269,13 +1407,13 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     else conv_in_kernel<2><<<grid1d(tot, 256), 256, 0, c.st>>>((const float*)x, w.w32, y, c.n, H, W, w.cout);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
-    return;
+    return false;
   }
   if (w.ks == 3 && !x_f32 && !res && w.cout == 1 && w.cin % 8 == 0) {
     conv_out_kernel<TA><<<grid1d(M, 256), 256, 9 * w.cin * sizeof(float), c.st>>>((const TA*)x, w.w32, y, c.n, H, W, w.cin, (const TA*)x_lo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
-    return;
+    return false;
   }
   dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((w.cout + CBN - 1) / CBN));
   if (w.ks == 3) {
@@ -1287,22 +1425,41 @@ void conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
   }
   if (c.u->prof) c.u->prof->end(pr, c.st);
   c.u->launches++;
+  return false;
 }
 
 // y (TA) = silu(gn(x)) or gn(x); copy (TA, optional) = x
+// With bs (block partials of x from the convolution that wrote it) the
+// statistics come from those instead of a pass over x.
 template <typename TA>
 void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = nullptr,
-        void* ylo = nullptr, void* copylo = nullptr) {
+        void* ylo = nullptr, void* copylo = nullptr, const float2* bs = nullptr) {
   if (!c.ok) return;
   const int G = c.u->d.groups;
   const double nb = (double)c.n * H * H * C;
-  // algorithmic bytes: statistics pass and apply pass each read the float32
-  // input once; the apply pass writes the operand (and the copy)
-  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (8.0 + sizeof(TA) * (copy ? 2 : 1))) : -1;
   const int HW = H * H;
   const int Cg = C / G;
   const int64_t units = (int64_t)c.n * HW * (C / 8);
-  if (C % 8 == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31)) {
+  const bool fast = C % 8 == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31);
+  const bool blk = fast && bs && C % 16 == 0 && Cg % 16 == 0 && HW % 32 == 0;
+  // algorithmic bytes: the apply pass reads the float32 input once and writes
+  // the operand (and the copy, and their low parts); without block partials
+  // a statistics pass reads the input once more
+  const double wr = (double)sizeof(TA) * (copy ? 2 : 1) * (ylo ? 2 : 1);
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * ((blk ? 4.0 : 8.0) + wr)) : -1;
+  if (blk) {
+    const BlkSrc src{nullptr, bs, 0, C, 0, HW / 32};
+    gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(src, c.n, G, c.u->stats);
+    const int upw = HW * (C / 8);
+    if (silu)
+      gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    else
+      gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches += 2;
+    return;
+  }
+  if (fast) {
     // each CTA reduces about 8192 values of one group
     const int Q = Cg / 4, P = 256 / Q;
     int chunk_px = std::max(P, 8192 / Cg);
@@ -1335,17 +1492,30 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
 // GroupNorm + SiLU of the virtual concat [up2(a), b]; writes the operand y and
 // the copy of the concat (the shortcut's operand), with low parts if split.
 // Returns false when the shape does not fit the fused kernels.
+// With bsa and bsb (block partials of a and b) the statistics come from
+// those instead of a pass over the concat.
 template <typename TA>
 bool gn_cat(Ctx& c, const float* a, int Ca, const float* b, int Cb, int H, void* y, void* copy, void* ylo,
-            void* copylo) {
+            void* copylo, const float2* bsa = nullptr, const float2* bsb = nullptr) {
   const int G = c.u->d.groups, C = Ca + Cb, Cg = C / G, HW = H * H;
   const int64_t units = (int64_t)c.n * HW * (C / 8);
   if (!(Ca % 8 == 0 && Cb % 8 == 0 && C % G == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31)))
     return false;
   if (!c.ok) return true;
+  const bool blk = bsa && bsb && Ca % 16 == 0 && Cb % 16 == 0 && Cg % 16 == 0 && (HW / 4) % 32 == 0;
   const double nb = (double)c.n * HW * C;
-  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (8.0 + sizeof(TA) * 2)) : -1;
+  const double wr = (double)sizeof(TA) * 2 * (ylo ? 2 : 1);
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * ((blk ? 4.0 : 8.0) + wr)) : -1;
   CatSrc src{a, b, Ca, Cb, H};
+  if (blk) {
+    const BlkSrc bsrc{bsa, bsb, Ca, Cb, HW / 128, HW / 32};
+    gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(bsrc, c.n, G, c.u->stats);
+    gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
+                                                                         (TA*)copy, (TA*)ylo, (TA*)copylo);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches += 2;
+    return true;
+  }
   const int Q = Cg / 4, P = 256 / Q;
   int chunk_px = std::max(P, 8192 / Cg);
   int chunks = (HW + chunk_px - 1) / chunk_px;
@@ -1364,26 +1534,32 @@ bool gn_cat(Ctx& c, const float* a, int Ca, const float* b, int Cb, int H, void*
 
 // Decoder ResBlock on the virtual concat [up2(a), b] (channels always change,
 // so the residual is the 1x1 shortcut of the concat).
+// bsa, bsb: block partials of a and b (or null); bsY: where to write those of
+// Y.  *y_stats tells whether they were written.
 template <typename TA>
 bool resblock_cat(Ctx& c, size_t& wi, const LevelBufs& lb, const float* a, int Ca, const float* b, int Cb,
-                  int cout, float* Y) {
+                  int cout, float* Y, const float2* bsa, const float2* bsb, float2* bsY, bool* y_stats) {
   const bool sp = c.u->split;
   if (Ca + Cb == cout) return false;
-  if (!gn_cat<TA>(c, a, Ca, b, Cb, lb.H, lb.T1, lb.T4, sp ? lb.T1lo : nullptr, sp ? lb.T4lo : nullptr))
+  if (!gn_cat<TA>(c, a, Ca, b, Cb, lb.H, lb.T1, lb.T4, sp ? lb.T1lo : nullptr, sp ? lb.T4lo : nullptr, bsa,
+                  bsb))
     return false;
   const ConvW& c1 = c.u->convs[wi++];
   const ConvW& c2 = c.u->convs[wi++];
   const ConvW& sk = c.u->convs[wi++];
-  conv_run<TA>(c, c1, lb.T1, false, nullptr, (float*)lb.T2, lb.H, sp ? lb.T1lo : nullptr);
+  const bool s2 = conv_run<TA>(c, c1, lb.T1, false, nullptr, (float*)lb.T2, lb.H, sp ? lb.T1lo : nullptr, lb.bT2);
   conv_run<TA>(c, sk, lb.T4, false, nullptr, (float*)lb.T3, lb.H, sp ? lb.T4lo : nullptr);
-  gn<TA>(c, (const float*)lb.T2, lb.H, cout, lb.T1, true, nullptr, sp ? lb.T1lo : nullptr);
-  conv_run<TA>(c, c2, lb.T1, false, (const float*)lb.T3, Y, lb.H, sp ? lb.T1lo : nullptr);
+  gn<TA>(c, (const float*)lb.T2, lb.H, cout, lb.T1, true, nullptr, sp ? lb.T1lo : nullptr, nullptr,
+         s2 ? lb.bT2 : nullptr);
+  *y_stats = conv_run<TA>(c, c2, lb.T1, false, (const float*)lb.T3, Y, lb.H, sp ? lb.T1lo : nullptr, bsY);
   return true;
 }
 
-// ResBlock: X (cin, float32) -> Y (cout, float32).
+// ResBlock: X (cin, float32) -> Y (cout, float32).  bsX: block partials of X
+// (or null); bsY: where to write those of Y; returns whether they were.
 template <typename TA>
-void resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, int cout, float* Y) {
+bool resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, int cout, float* Y,
+              const float2* bsX = nullptr, float2* bsY = nullptr) {
   const ConvW& c1 = c.u->convs[wi++];
   const ConvW& c2 = c.u->convs[wi++];
   const ConvW* sk = nullptr;
@@ -1391,16 +1567,17 @@ void resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
   const bool need_copy = sk && !std::is_same<TA, float>::value;
   const bool sp = c.u->split;
   gn<TA>(c, X, b.H, cin, b.T1, true, need_copy ? b.T4 : nullptr, sp ? b.T1lo : nullptr,
-         sp && need_copy ? b.T4lo : nullptr);
-  conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H, sp ? b.T1lo : nullptr);
+         sp && need_copy ? b.T4lo : nullptr, bsX);
+  const bool s2 = conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H, sp ? b.T1lo : nullptr, b.bT2);
   const float* res = X;
   if (sk) {
     if (need_copy) conv_run<TA>(c, *sk, b.T4, false, nullptr, (float*)b.T3, b.H, sp ? b.T4lo : nullptr);
     else conv_run<TA>(c, *sk, X, true, nullptr, (float*)b.T3, b.H);
     res = (const float*)b.T3;
   }
-  gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true, nullptr, sp ? b.T1lo : nullptr);
-  conv_run<TA>(c, c2, b.T1, false, res, Y, b.H, sp ? b.T1lo : nullptr);
+  gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true, nullptr, sp ? b.T1lo : nullptr, nullptr,
+         s2 ? b.bT2 : nullptr);
+  return conv_run<TA>(c, c2, b.T1, false, res, Y, b.H, sp ? b.T1lo : nullptr, bsY);
 }
 
 template <typename TA>
@@ -1411,9 +1588,11 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   size_t wi = 0;
   conv_run<TA>(c, u->convs[wi++], x_in, true, nullptr, (float*)u->lv[0].P, d.window);
   int prev = d.ch[0];
+  // which of SK / M hold block partials written by their convolution
+  bool sk_st[8] = {false}, m_st[8] = {false};
   for (int l = 0; l < L; ++l) {
     LevelBufs& b = u->lv[l];
-    resblock<TA>(c, wi, b, (const float*)b.P, prev, d.ch[l], (float*)b.SK);
+    sk_st[l] = resblock<TA>(c, wi, b, (const float*)b.P, prev, d.ch[l], (float*)b.SK, nullptr, b.bSK);
     prev = d.ch[l];
     if (l < L - 1) {
       const int64_t tot = (int64_t)n * (b.H / 2) * (b.H / 2) * prev;
@@ -1428,10 +1607,11 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   }
   LevelBufs& bl = u->lv[L - 1];
   const float* cur = (const float*)bl.SK;
+  const float2* cur_bs = sk_st[L - 1] ? bl.bSK : nullptr;
   if (d.attn) {
     const ConvW& qkv = u->convs[wi++];
     const ConvW& proj = u->convs[wi++];
-    gn<TA>(c, cur, bl.H, prev, bl.T1, false, nullptr, u->split ? bl.T1lo : nullptr);
+    gn<TA>(c, cur, bl.H, prev, bl.T1, false, nullptr, u->split ? bl.T1lo : nullptr, nullptr, cur_bs);
     conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H, u->split ? bl.T1lo : nullptr);
     const int Tn = bl.H * bl.H, dh = prev / d.heads;
     const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
@@ -1448,14 +1628,17 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     }
     if (u->prof) u->prof->end(pr, st);
     u->launches++;
-    conv_run<TA>(c, proj, bl.T3, false, cur, (float*)bl.CAT, bl.H, u->split ? bl.T3lo : nullptr);
+    const bool cs = conv_run<TA>(c, proj, bl.T3, false, cur, (float*)bl.CAT, bl.H,
+                                 u->split ? bl.T3lo : nullptr, bl.bCAT);
     cur = (const float*)bl.CAT;
+    cur_bs = cs ? bl.bCAT : nullptr;
   }
-  resblock<TA>(c, wi, bl, cur, prev, prev, (float*)bl.M);
+  m_st[L - 1] = resblock<TA>(c, wi, bl, cur, prev, prev, (float*)bl.M, cur_bs, bl.bM);
   for (int l = L - 2; l >= 0; --l) {
     LevelBufs& b = u->lv[l];
     if (resblock_cat<TA>(c, wi, b, (const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], d.ch[l],
-                         (float*)b.M)) {
+                         (float*)b.M, m_st[l + 1] ? u->lv[l + 1].bM : nullptr, sk_st[l] ? b.bSK : nullptr,
+                         b.bM, &m_st[l])) {
       prev = d.ch[l];
       continue;
     }
@@ -1471,7 +1654,8 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     prev = d.ch[l];
   }
   LevelBufs& b0 = u->lv[0];
-  gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true, nullptr, u->split ? b0.T1lo : nullptr);
+  gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true, nullptr, u->split ? b0.T1lo : nullptr, nullptr,
+         m_st[0] ? b0.bM : nullptr);
   conv_run<TA>(c, u->convs[wi++], b0.T1, false, nullptr, F, d.window, u->split ? b0.T1lo : nullptr);
   if (c.ok) {
     cudaError_t e = cudaGetLastError();
