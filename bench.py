@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="idf", choices=["idf", "reference"])
     p.add_argument("--query", type=int, default=QUERY)
-    p.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "fp32"])
+    p.add_argument("--precision", default="bf16x3", choices=["bf16", "bf16x3", "tf32", "fp32"])
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
     p.add_argument("--student", type=int, default=0,
@@ -279,13 +279,16 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- idf arm
 
-def traffic_record():
+def traffic_record(precision: str):
     """Per-launch DRAM traffic of the tensor-core conv from a committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary, valid only while the kernel source is unchanged and for the
+    precision it was captured at."""
     p = os.path.join(ROOT, "profiles", "conv_tc_traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
+    if rec.get("precision", "bf16x3") != precision:
+        return None
     src = open(os.path.join(ROOT, "paper_2512_08309_gb300", "csrc", "conv_tc.cu"), "rb").read()
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
@@ -359,13 +362,19 @@ def run_idf(args, rank, world, local):
     tc = prof["conv_tc"]
     achieved = tc["flops"] / (tc["ms"] / 1000.0) / 1e12 if tc["ms"] > 0 else 0.0
     peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-    rec = traffic_record()
+    peak_kind = f"{pk_kind} bf16 sustained"
+    if args.precision == "tf32":
+        # the contraction's own dtype: the measured bf16 peak x the nominal
+        # dense tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
+        peak = peak * 1.1 / 2.25
+        peak_kind = f"{pk_kind} bf16 sustained x 1.1/2.25 (tf32)"
+    rec = traffic_record(args.precision)
     fpl = tc["flops"] / max(1, tc["launches"])
     # bf16x3 issues three bf16 products per multiply-add of the convolution
     mma_factor = 3.0 if args.precision == "bf16x3" else 1.0
     roofline = {"kernel": "conv_tc (tcgen05 implicit-GEMM conv)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_kind": f"{pk_kind} bf16 sustained",
+                "peak_kind": peak_kind,
                 "mma_work_factor": mma_factor, "achieved_mma": achieved * mma_factor,
                 "frac_mma": achieved * mma_factor / peak,
                 # DRAM bytes per algorithmic FLOP from the committed ncu capture of the
@@ -386,7 +395,8 @@ def run_idf(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32"}.get(args.precision, "bf16"),
+        "data": "synthetic",
         "config": bench_config(q, args.precision, {"coarse": wins[0] / args.steps, "fine": wins[1] / args.steps},
                                world),
         "gpu_launches": launches, "output_finite": finite,
@@ -417,7 +427,7 @@ def run_idf(args, rank, world, local):
     if not args.no_fp32 and rank == 0:
         nf, nc = window_counts(st, q)
         res = {}
-        for prec, nb in (("fp32", 8), ("bf16", 64), ("bf16x3", 64)):
+        for prec, nb in (("fp32", 8), ("bf16", 64), ("bf16x3", 64), ("tf32", 64)):
             Wp = idf.World(0, st, wts, precision=prec, max_batch=nb)
             t_lv = []
             for li, n_win in ((1, nb), (0, nb)):
@@ -441,6 +451,7 @@ def run_idf(args, rank, world, local):
                                         "final px of this workload",
                               "bf16_same_method": res["bf16"]["px_s"],
                               "bf16x3_same_method": res["bf16x3"]["px_s"],
+                              "tf32_same_method": res["tf32"]["px_s"],
                               "speedup_bf16_vs_fp32_unet": res["bf16"]["px_s"] / res["fp32"]["px_s"],
                               "speedup_bf16x3_vs_fp32_unet": res["bf16x3"]["px_s"] / res["fp32"]["px_s"],
                               "detail": res}

@@ -55,8 +55,11 @@ typedef enum {
  * accumulation, float32 residual stream.  IDF_BF16X3: the same tensor-core
  * path with each operand split as hi + lo (both bfloat16) and the products
  * hi*hi + lo*hi + hi*lo accumulated, which compensates the rounding of both
- * operands at three times the tensor work.  IDF_FP8_E4M3 is not built yet. */
-typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2, IDF_BF16X3 = 3 } idf_precision;
+ * operands at three times the tensor work.  IDF_TF32: operands rounded to
+ * tf32 (10 explicit mantissa bits, round to nearest even) and one tensor-core
+ * product per multiply-add (kind::tf32, half the bf16 rate), float32
+ * accumulation and residual stream.  IDF_FP8_E4M3 is not built yet. */
+typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2, IDF_BF16X3 = 3, IDF_TF32 = 4 } idf_precision;
 
 typedef enum {
   IDF_OUT_MODEL = 0,  /* the last level's final sample J_K in model units */

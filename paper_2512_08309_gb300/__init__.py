@@ -19,10 +19,10 @@ IDF_OK, IDF_EINVAL, IDF_ENOMEM, IDF_ECUDA, IDF_ETIMEOUT, IDF_EMODEL, IDF_EDEVICE
     IDF_EINTERNAL, IDF_EUNSUPPORTED = range(9)
 STATUS_NAMES = ["IDF_OK", "IDF_EINVAL", "IDF_ENOMEM", "IDF_ECUDA", "IDF_ETIMEOUT", "IDF_EMODEL",
                 "IDF_EDEVICE_CHECK", "IDF_EINTERNAL", "IDF_EUNSUPPORTED"]
-IDF_FP32, IDF_BF16, IDF_FP8_E4M3, IDF_BF16X3 = 0, 1, 2, 3
+IDF_FP32, IDF_BF16, IDF_FP8_E4M3, IDF_BF16X3, IDF_TF32 = 0, 1, 2, 3, 4
 IDF_OUT_MODEL, IDF_OUT_METRES = 0, 1
 
-PRECISIONS = {"fp32": IDF_FP32, "bf16": IDF_BF16, "fp8": IDF_FP8_E4M3, "bf16x3": IDF_BF16X3}
+PRECISIONS = {"fp32": IDF_FP32, "bf16": IDF_BF16, "fp8": IDF_FP8_E4M3, "bf16x3": IDF_BF16X3, "tf32": IDF_TF32}
 
 # Every symbol include/idf.h declares.
 EXPORTS = [

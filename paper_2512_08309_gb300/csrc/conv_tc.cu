@@ -19,11 +19,21 @@
 //              other accumulator with tcgen05.ld (warp w reads TMEM lanes
 //              32*(w%4)..+31) and write float32 NHWC output, adding the
 //              residual if given, while the next tile accumulates.
+//   TF32:      with float32 operands (IDF_TF32, values already rounded to
+//              tf32 by their producers) the same pipeline issues
+//              tcgen05.mma kind::tf32 (K = 8 per instruction); a stage then
+//              carries 32 channels, so its bytes and layout are those of a
+//              64-channel bfloat16 stage.
 //   Split:     with low parts given (IDF_BF16X3) a stage holds A_hi, A_lo,
 //              B_hi and B_lo and issues A_hi B_hi + A_lo B_hi + A_hi B_lo per
 //              K step, where x = hi + lo with hi = bf16(x), lo = bf16(x - hi):
 //              bfloat16 products with the rounding of both operands
 //              compensated.
+//   Fold:      optionally the tile's K loop continues over a second operand,
+//              a 1x1 convolution of another tensor (the ResBlock shortcut)
+//              accumulated into the same TMEM tile: one 128-pixel box and
+//              one weight box per 64 input channels, from its own tensor
+//              maps.  The shortcut's output never goes through memory.
 //   Stats:     optionally the epilogue also emits GroupNorm partials of the
 //              values it writes: per 32-pixel block (one warp's TMEM lanes)
 //              and 16-channel slice, the mean and the sum of squared
@@ -123,9 +133,12 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: bf16 x bf16 -> f32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: f32 accumulator (bits 4-5 = 1), A and B formats
+// (bits 7-9, 10-12: 1 = bf16 under kind::f16, 2 = tf32 under kind::tf32),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_mma(int M, int N, bool tf32) {
+  return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
@@ -136,6 +149,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// One K step of 32 bytes per operand row: 16 bf16 or 8 tf32 values.
+template <bool TF32>
+__device__ __forceinline__ void mma_step(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  if (TF32) mma_tf32(tmem_d, adesc, bdesc, idesc, accumulate);
+  else mma_bf16(tmem_d, adesc, bdesc, idesc, accumulate);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -171,6 +202,8 @@ struct TcParams {
   float2* bstats;  // null, or (mean, M2) per (32-pixel block, 16-channel slice)
   int* status;
   int H, W, Cout, ks, n_kc, n_iter;
+  int kch;               // input channels per K stage (64 bf16 or 32 tf32: 128 bytes)
+  int n_iter1;           // K iterations of the main operand; the rest are the folded 1x1 operand
   int m_tiles, n_tiles;  // output tiles: 128-pixel rows x BN channels
 };
 
@@ -183,11 +216,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // L2).  The shared-memory ring of STAGES stages runs across tile boundaries;
 // two TMEM accumulators (2 x BN columns) let the epilogue of one tile overlap
 // the main loop of the next.
-template <int BN, int STAGES, bool SPLIT, bool DXR>
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmA_lo,
                                                          const __grid_constant__ CUtensorMap tmB_lo,
+                                                         const __grid_constant__ CUtensorMap tmA2,
+                                                         const __grid_constant__ CUtensorMap tmB2,
+                                                         const __grid_constant__ CUtensorMap tmA2_lo,
+                                                         const __grid_constant__ CUtensorMap tmB2_lo,
                                                          TcParams p) {
   // DXR (3x3 convs on 128-pixel rows): a stage holds one kernel row dy: a
   // 130-pixel activation box (halo columns zero-filled) read by the three
@@ -199,6 +236,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
   constexpr int NP = SPLIT ? 2 : 1;                         // hi (and lo) parts per operand
   constexpr int STAGE_BYTES = NP * (A_BYTES + NB * B_BYTES);
   constexpr int TX_BYTES = NP * (A_BOX + NB * B_BYTES);
+  constexpr int TX2_BYTES = NP * (BM * 128 + B_BYTES);      // a folded 1x1 stage
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -241,6 +279,14 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA_lo) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB_lo) : "memory");
     }
+    if (p.n_iter > p.n_iter1) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA2) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB2) : "memory");
+      if (SPLIT) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA2_lo) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB2_lo) : "memory");
+      }
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -274,24 +320,35 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           }
           uint8_t* a = smem + (size_t)s * STAGE_BYTES;
           uint8_t* b = a + NP * A_BYTES;
-          mbar_expect_tx(&full_bar[s], TX_BYTES);
-          if (DXR) {
+          if (kk >= p.n_iter1) {
+            // folded 1x1 operand: the tile's own pixels, 64 channels
+            const int kc = kk - p.n_iter1;
+            mbar_expect_tx(&full_bar[s], TX2_BYTES);
+            tma_load_4d(a, &tmA2, &full_bar[s], kc * p.kch, 0, y0, win);
+            tma_load_2d(b, &tmB2, &full_bar[s], kc * p.kch, n0);
+            if (SPLIT) {
+              tma_load_4d(a + A_BYTES, &tmA2_lo, &full_bar[s], kc * p.kch, 0, y0, win);
+              tma_load_2d(b + NB * B_BYTES, &tmB2_lo, &full_bar[s], kc * p.kch, n0);
+            }
+          } else if (DXR) {
+            mbar_expect_tx(&full_bar[s], TX_BYTES);
             const int dyi = kk / p.n_kc, kc = kk % p.n_kc;
-            tma_load_4d(a, &tmA, &full_bar[s], kc * 64, -1, y0 + dyi - 1, win);
-            if (SPLIT) tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * 64, -1, y0 + dyi - 1, win);
+            tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, -1, y0 + dyi - 1, win);
+            if (SPLIT) tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * p.kch, -1, y0 + dyi - 1, win);
             for (int t = 0; t < 3; ++t) {
-              tma_load_2d(b + t * B_BYTES, &tmB, &full_bar[s], kc * 64, (dyi * 3 + t) * p.Cout + n0);
+              tma_load_2d(b + t * B_BYTES, &tmB, &full_bar[s], kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
               if (SPLIT)
-                tma_load_2d(b + (3 + t) * B_BYTES, &tmB_lo, &full_bar[s], kc * 64, (dyi * 3 + t) * p.Cout + n0);
+                tma_load_2d(b + (3 + t) * B_BYTES, &tmB_lo, &full_bar[s], kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
             }
           } else {
+            mbar_expect_tx(&full_bar[s], TX_BYTES);
             const int tap = kk / p.n_kc, kc = kk % p.n_kc;
             const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
-            tma_load_4d(a, &tmA, &full_bar[s], kc * 64, dx, y0 + dy, win);
-            tma_load_2d(b, &tmB, &full_bar[s], kc * 64, tap * p.Cout + n0);
+            tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, dx, y0 + dy, win);
+            tma_load_2d(b, &tmB, &full_bar[s], kc * p.kch, tap * p.Cout + n0);
             if (SPLIT) {
-              tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * 64, dx, y0 + dy, win);
-              tma_load_2d(b + B_BYTES, &tmB_lo, &full_bar[s], kc * 64, tap * p.Cout + n0);
+              tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * p.kch, dx, y0 + dy, win);
+              tma_load_2d(b + B_BYTES, &tmB_lo, &full_bar[s], kc * p.kch, tap * p.Cout + n0);
             }
           }
           last_issue[s] = (int)it;
@@ -306,7 +363,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      constexpr uint32_t idesc = idesc_mma(BM, BN, TF32);
       uint32_t it = 0, acc = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++acc) {
@@ -324,6 +381,19 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           fence_after();
           const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
           const uint32_t b = a + NP * A_BYTES;
+          if (kk >= p.n_iter1) {
+            // folded 1x1 operand (never the first K step of a tile)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              mma_step<TF32>(d, umma_desc(a + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
+              if (SPLIT) {
+                mma_step<TF32>(d, umma_desc(a + A_BYTES + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
+                mma_step<TF32>(d, umma_desc(a + 32 * k), umma_desc(b + NB * B_BYTES + 32 * k), idesc, 1u);
+              }
+            }
+            mma_commit(&empty_bar[s]);
+            continue;
+          }
 #pragma unroll
           for (int t = 0; t < NB; ++t) {
             // DXR: horizontal tap t reads the staged rows starting at row t
@@ -331,11 +401,11 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             const uint32_t bt = b + B_BYTES * t;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              mma_bf16(d, umma_desc(at + 32 * k), umma_desc(bt + 32 * k), idesc,
+              mma_step<TF32>(d, umma_desc(at + 32 * k), umma_desc(bt + 32 * k), idesc,
                        (kk > 0 || t > 0 || k > 0) ? 1u : 0u);
               if (SPLIT) {
-                mma_bf16(d, umma_desc(at + A_BYTES + 32 * k), umma_desc(bt + 32 * k), idesc, 1u);
-                mma_bf16(d, umma_desc(at + 32 * k), umma_desc(bt + NB * B_BYTES + 32 * k), idesc, 1u);
+                mma_step<TF32>(d, umma_desc(at + A_BYTES + 32 * k), umma_desc(bt + 32 * k), idesc, 1u);
+                mma_step<TF32>(d, umma_desc(at + 32 * k), umma_desc(bt + NB * B_BYTES + 32 * k), idesc, 1u);
               }
             }
           }
@@ -443,13 +513,17 @@ int sm_count() {
   return n;
 }
 
-template <int BN, int STAGES, bool SPLIT, bool DXR>
-bool launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, const CUtensorMap& blo,
-            const TcParams& p, cudaStream_t st, std::string* err) {
+struct Maps {
+  CUtensorMap a, b, alo, blo;      // main operand (and low parts)
+  CUtensorMap a2, b2, a2lo, b2lo;  // folded 1x1 operand (copies of the above when absent)
+};
+
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32 = false>
+bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err) {
   const size_t smem = (size_t)STAGES * (SPLIT ? 2 : 1) * ((DXR ? 17 * 1024 : BM * 128) + (DXR ? 3 : 1) * BN * 128) + 1024;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, SPLIT, DXR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
       *err = "cudaFuncSetAttribute failed";
       return false;
@@ -458,7 +532,8 @@ bool launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, 
   }
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sm_count() ? tiles : sm_count();
-  conv_tc_kernel<BN, STAGES, SPLIT, DXR><<<grid, 192, smem, st>>>(a, b, alo, blo, p);
+  conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32><<<grid, 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo,
+                                                                    m.b2lo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -478,11 +553,17 @@ bool conv_tc_shape_ok(int H, int W) {
   return W >= 1 && W <= 128 && 128 % W == 0 && ((int64_t)H * W) % 128 == 0 && 128 / W <= H;
 }
 
-bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16* w_lo, const float* res,
+bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void* w_lo, const float* res,
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
-                     cudaStream_t st, std::string* err) {
+                     cudaStream_t st, std::string* err, const void* x2, const void* w2, const void* x2_lo,
+                     const void* w2_lo, int Cin2, bool tf32) {
   if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
     *err = "shape not supported by the tensor-core convolution";
+    return false;
+  }
+  const bool fold = x2 != nullptr;
+  if (fold && (!w2 || !conv_tc_supported(Cin2, Cout, 1))) {
+    *err = "folded 1x1 operand not supported by the tensor-core convolution";
     return false;
   }
   auto enc = encode_fn();
@@ -492,38 +573,71 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
   }
   const int BN = Cout <= 256 ? Cout : 256;
   const bool split = x_lo && w_lo;
-  CUtensorMap ta, tb, ta_lo, tb_lo;
+  if (tf32 && split) {
+    *err = "tf32 operands have no low parts";
+    return false;
+  }
+  // one K stage reads 128 bytes of channels per pixel / weight row
+  const int es = tf32 ? 4 : 2, kch = 128 / es;
+  const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (fold && split != (x2_lo && w2_lo)) {
+    *err = "folded operand low parts must be given exactly when the main operand's are";
+    return false;
+  }
+  Maps m;
   // 3x3 convs on 128-pixel rows stage one 130-pixel box per kernel row
   const bool dxr = ks == 3 && W == 128 && BN == 64;
-  auto encA = [&](CUtensorMap* m, const bf16* ptr) {
-    cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
-    cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)(dxr ? W + 2 : W), (cuuint32_t)(dxr ? 1 : 128 / W), 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)ptr, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  // activations (n, H, W, C); box of kch channels x bw pixels x bh rows
+  auto encA = [&](CUtensorMap* mp, const void* ptr, int C, int bw, int bh) {
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    cuuint64_t strides[3] = {(cuuint64_t)C * es, (cuuint64_t)W * C * es, (cuuint64_t)H * W * C * es};
+    cuuint32_t box[4] = {(cuuint32_t)kch, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    cuuint32_t ones[4] = {1, 1, 1, 1};
+    return enc(mp, dt, 4, (void*)ptr, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  auto encB = [&](CUtensorMap* m, const bf16* ptr) {
-    cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)ks * ks * Cout};
-    cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)BN};
-    cuuint32_t es[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  // weights [tap][Cout][C]; box of kch channels x BN rows
+  auto encB = [&](CUtensorMap* mp, const void* ptr, int C, int taps) {
+    cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)taps * Cout};
+    cuuint64_t strides[1] = {(cuuint64_t)C * es};
+    cuuint32_t box[2] = {(cuuint32_t)kch, (cuuint32_t)BN};
+    cuuint32_t ones[2] = {1, 1};
+    return enc(mp, dt, 2, (void*)ptr, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  if (split && (!encA(&ta_lo, x_lo) || !encB(&tb_lo, w_lo))) {
+  const int abw = dxr ? W + 2 : W, abh = dxr ? 1 : 128 / W;
+  if (!encA(&m.a, x, Cin, abw, abh) || !encB(&m.b, w, Cin, ks * ks)) {
+    *err = "tensor map (activations or weights) encode failed";
+    return false;
+  }
+  if (split && (!encA(&m.alo, x_lo, Cin, abw, abh) || !encB(&m.blo, w_lo, Cin, ks * ks))) {
     *err = "tensor map (low parts) encode failed";
     return false;
   }
-  if (!encA(&ta, x)) {
-    *err = "tensor map (activations) encode failed";
-    return false;
+  if (!split) {
+    m.alo = m.a;
+    m.blo = m.b;
   }
-  if (!encB(&tb, w)) {
-    *err = "tensor map (weights) encode failed";
-    return false;
+  if (fold) {
+    if (!encA(&m.a2, x2, Cin2, W, 128 / W) || !encB(&m.b2, w2, Cin2, 1)) {
+      *err = "tensor map (folded operand) encode failed";
+      return false;
+    }
+    if (split && (!encA(&m.a2lo, x2_lo, Cin2, W, 128 / W) || !encB(&m.b2lo, w2_lo, Cin2, 1))) {
+      *err = "tensor map (folded operand low parts) encode failed";
+      return false;
+    }
+    if (!split) {
+      m.a2lo = m.a2;
+      m.b2lo = m.b2;
+    }
+  } else {
+    m.a2 = m.a;
+    m.b2 = m.b;
+    m.a2lo = m.alo;
+    m.b2lo = m.blo;
   }
   TcParams p;
   p.res = res;
@@ -534,32 +648,31 @@ bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16*
   p.W = W;
   p.Cout = Cout;
   p.ks = ks;
-  p.n_kc = Cin / 64;
-  p.n_iter = (dxr && BN == 64 ? ks : ks * ks) * (Cin / 64);
+  p.kch = kch;
+  p.n_kc = Cin / kch;
+  p.n_iter1 = (dxr ? ks : ks * ks) * p.n_kc;
+  p.n_iter = p.n_iter1 + (fold ? Cin2 / kch : 0);
   p.m_tiles = (int)((int64_t)n * H * W / BM);
   p.n_tiles = Cout / BN;
-  if (!split) {
-    ta_lo = ta;
-    tb_lo = tb;
-  }
   // stages: about 192 KB of shared memory per CTA, one CTA per SM
-  if (dxr && BN != 64) {
-    *err = "row-reuse staging is built for 64-channel tiles only";
-    return false;
-  }
-  if (!split) {
+  if (tf32) {
     switch (BN) {
-      case 64: return dxr ? launch<64, 5, false, true>(ta, tb, ta_lo, tb_lo, p, st, err)
-                          : launch<64, 8, false, false>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 128: return launch<128, 6, false, false>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 256: return launch<256, 4, false, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 64: return dxr ? launch<64, 5, false, true, true>(m, p, st, err)
+                          : launch<64, 8, false, false, true>(m, p, st, err);
+      case 128: return launch<128, 6, false, false, true>(m, p, st, err);
+      case 256: return launch<256, 4, false, false, true>(m, p, st, err);
+    }
+  } else if (!split) {
+    switch (BN) {
+      case 64: return dxr ? launch<64, 5, false, true>(m, p, st, err) : launch<64, 8, false, false>(m, p, st, err);
+      case 128: return launch<128, 6, false, false>(m, p, st, err);
+      case 256: return launch<256, 4, false, false>(m, p, st, err);
     }
   } else {
     switch (BN) {
-      case 64: return dxr ? launch<64, 2, true, true>(ta, tb, ta_lo, tb_lo, p, st, err)
-                          : launch<64, 4, true, false>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 128: return launch<128, 3, true, false>(ta, tb, ta_lo, tb_lo, p, st, err);
-      case 256: return launch<256, 2, true, false>(ta, tb, ta_lo, tb_lo, p, st, err);
+      case 64: return dxr ? launch<64, 2, true, true>(m, p, st, err) : launch<64, 4, true, false>(m, p, st, err);
+      case 128: return launch<128, 3, true, false>(m, p, st, err);
+      case 256: return launch<256, 2, true, false>(m, p, st, err);
     }
   }
   *err = "unsupported N tile";

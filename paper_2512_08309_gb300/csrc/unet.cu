@@ -37,12 +37,29 @@
 namespace idf {
 
 // ------------------------------------------------------------------ helpers
+// Operand type of IDF_TF32: a float32 value already rounded to tf32 (10
+// explicit mantissa bits) when it is stored, so that the tensor cores'
+// kind::tf32 products see exactly the stored value.
+struct tf32 {
+  float f;
+};
+
+// Round to nearest, ties to even, at mantissa bit 13 (finite values).
+__host__ __device__ __forceinline__ uint32_t tf32_rn_bits(uint32_t u) {
+  if ((u & 0x7f800000u) == 0x7f800000u) return u;
+  u += 0xfffu + ((u >> 13) & 1u);
+  return u & 0xffffe000u;
+}
+__device__ __forceinline__ float tf32_rn(float v) { return __uint_as_float(tf32_rn_bits(__float_as_uint(v))); }
+
 template <typename T> __device__ __forceinline__ float ld(const T* p);
 template <> __device__ __forceinline__ float ld<float>(const float* p) { return *p; }
 template <> __device__ __forceinline__ float ld<bf16>(const bf16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float ld<tf32>(const tf32* p) { return p->f; }
 template <typename T> __device__ __forceinline__ void st(T* p, float v);
 template <> __device__ __forceinline__ void st<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void st<bf16>(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ void st<tf32>(tf32* p, float v) { p->f = tf32_rn(v); }
 
 static int grid1d(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
@@ -374,6 +391,12 @@ template <> struct Pack8<float> {
     reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
   }
 };
+template <> struct Pack8<tf32> {
+  static __device__ __forceinline__ void store(tf32* p, const float (&v)[8]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(tf32_rn(v[0]), tf32_rn(v[1]), tf32_rn(v[2]), tf32_rn(v[3]));
+    reinterpret_cast<float4*>(p)[1] = make_float4(tf32_rn(v[4]), tf32_rn(v[5]), tf32_rn(v[6]), tf32_rn(v[7]));
+  }
+};
 template <> struct Pack8<bf16> {
   static __device__ __forceinline__ void store(bf16* p, const float (&v)[8]) {
     uint4 u;
@@ -584,6 +607,11 @@ template <> struct Load8<float> {
   static __device__ __forceinline__ void load(const float* p, float (&v)[8]) {
     const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+template <> struct Load8<tf32> {
+  static __device__ __forceinline__ void load(const tf32* p, float (&v)[8]) {
+    Load8<float>::load(reinterpret_cast<const float*>(p), v);
   }
 };
 template <> struct Load8<bf16> {
@@ -1079,9 +1107,10 @@ __global__ void attention_kernel(const float* __restrict__ qkv, int Tn, int C, i
 }
 
 // ------------------------------------------------------------ engine
-bool conv_tc_forward(const bf16* x, const bf16* w, const bf16* x_lo, const bf16* w_lo, const float* res,
+bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void* w_lo, const float* res,
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
-                     cudaStream_t st, std::string* err);
+                     cudaStream_t st, std::string* err, const void* x2 = nullptr, const void* w2 = nullptr,
+                     const void* x2_lo = nullptr, const void* w2_lo = nullptr, int Cin2 = 0, bool tf32 = false);
 bool conv_tc_shape_ok(int H, int W);
 
 struct ConvW {
@@ -1089,6 +1118,7 @@ struct ConvW {
   float* w32 = nullptr;  // [K][Cout], k = tap*Cin + ci
   bf16* w16 = nullptr;   // [tap][Cout][Cin] (tensor-core layout) or null
   bf16* w16lo = nullptr; // low parts of the same (IDF_BF16X3) or null
+  float* wtf = nullptr;  // [tap][Cout][Cin] rounded to tf32 (IDF_TF32) or null
   bool tc = false;
 };
 
@@ -1199,6 +1229,7 @@ void unet_destroy(UNet* u) {
     cudaFree(c.w32);
     cudaFree(c.w16);
     cudaFree(c.w16lo);
+    cudaFree(c.wtf);
   }
   if (u->own_bufs)
     for (auto& b : u->lv) {
@@ -1234,6 +1265,7 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
   u->split = precision == 3;
   u->max_batch = std::max(1, max_batch);
   const bool bfm = precision == 1 || precision == 3;
+  const bool tfm = precision == 4;
   auto shapes = unet_param_shapes(d);
   size_t off = 0;
   // resolution of each conv, to know whether the tensor-core kernel applies
@@ -1269,6 +1301,22 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
         if (!ck(cudaMalloc(&c.w16lo, p16lo.size() * 2), err, "cudaMalloc bf16 weights")) { unet_destroy(u); return nullptr; }
         if (!ck(cudaMemcpy(c.w16lo, p16lo.data(), p16lo.size() * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")) { unet_destroy(u); return nullptr; }
       }
+      c.tc = true;
+    }
+    if (tfm && conv_tc_supported(c.cin, c.cout, c.ks)) {
+      // (Cout, Cin, kh, kw) -> [tap][Cout][Cin] float32 rounded to tf32
+      std::vector<float> pt((size_t)taps * c.cout * c.cin);
+      for (int o = 0; o < c.cout; ++o)
+        for (int ci = 0; ci < c.cin; ++ci)
+          for (int t = 0; t < taps; ++t) {
+            uint32_t u;
+            const float v = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
+            std::memcpy(&u, &v, 4);
+            u = tf32_rn_bits(u);
+            std::memcpy(&pt[((size_t)t * c.cout + o) * c.cin + ci], &u, 4);
+          }
+      if (!ck(cudaMalloc(&c.wtf, pt.size() * 4), err, "cudaMalloc tf32 weights")) { unet_destroy(u); return nullptr; }
+      if (!ck(cudaMemcpy(c.wtf, pt.data(), pt.size() * 4, cudaMemcpyHostToDevice), err, "copy tf32 weights")) { unet_destroy(u); return nullptr; }
       c.tc = true;
     }
     off += (size_t)c.cout * c.cin * taps;
@@ -1340,23 +1388,38 @@ struct Ctx {
   bool ok = true;
 };
 
+// Whether conv_run takes the tensor-core path for w at resolution H.
+template <typename TA>
+bool tc_path(const ConvW& w, int H) {
+  return !std::is_same<TA, float>::value && w.tc && conv_tc_shape_ok(H, H);
+}
+
 // out (float32) = conv(x) (+ res), x in operand type TA (or float32 x_f32).
 // With bs given, the tensor-core path also writes the GroupNorm block
-// partials of out there; returns whether it did.
+// partials of out there; returns whether it did.  With w2 given (tensor-core
+// path only: the caller checks tc_path for both), the 1x1 convolution w2 of
+// x2 is accumulated into the same output tiles.
 template <typename TA>
 bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H,
-              const void* x_lo = nullptr, float2* bs = nullptr) {
+              const void* x_lo = nullptr, float2* bs = nullptr, const ConvW* w2 = nullptr,
+              const void* x2 = nullptr, const void* x2_lo = nullptr) {
   if (!c.ok) return false;
   const int W = H;
-  const double flops = 2.0 * c.n * H * W * (double)w.cout * w.ks * w.ks * w.cin;
-  if (std::is_same<TA, bf16>::value && w.tc && !x_f32 && conv_tc_shape_ok(H, W)) {
+  const double flops = 2.0 * c.n * H * W * (double)w.cout * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0));
+  if (tc_path<TA>(w, H) && !x_f32) {
     std::string e;
-    // algorithmic bytes: bf16 operand read once, weights, float32 output (+ residual)
-    const double by = c.n * H * W * (2.0 * w.cin + 4.0 * w.cout * (res ? 2 : 1)) + 2.0 * w.ks * w.ks * w.cin * w.cout;
+    // algorithmic bytes: bf16 operands read once, weights, float32 output (+ residual)
+    const double by = c.n * H * W * (2.0 * (w.cin + (w2 ? w2->cin : 0)) + 4.0 * w.cout * (res ? 2 : 1)) +
+                      2.0 * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0)) * w.cout;
     const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
-    const bool ok = conv_tc_forward((const bf16*)x, w.w16, c.u->split ? (const bf16*)x_lo : nullptr,
-                                    c.u->split ? w.w16lo : nullptr, res, y, bs, c.n, H, W, w.cin, w.cout,
-                                    w.ks, c.u->status, c.st, &e);
+    const bool sp = c.u->split;
+    const bool tf = std::is_same<TA, tf32>::value;
+    const void* wk = tf ? (const void*)w.wtf : (const void*)w.w16;
+    const void* wk2 = w2 ? (tf ? (const void*)w2->wtf : (const void*)w2->w16) : nullptr;
+    const bool ok = conv_tc_forward(x, wk, sp ? x_lo : nullptr, sp ? w.w16lo : nullptr, res, y, bs, c.n, H, W,
+                                    w.cin, w.cout, w.ks, c.u->status, c.st, &e, w2 ? x2 : nullptr, wk2,
+                                    w2 && sp ? x2_lo : nullptr, w2 && sp ? w2->w16lo : nullptr,
+                                    w2 ? w2->cin : 0, tf);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     if (!ok) {
       c.ok = false;
@@ -1365,6 +1428,12 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     }
     c.u->launches++;
     return ok && bs != nullptr;
+  }
+  if (w2) {
+    c.ok = false;
+    c.err->code = 3;
+    c.err->msg = "folded 1x1 operand outside the tensor-core path";
+    return false;
   }
   const int64_t M = (int64_t)c.n * H * W;
   const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, flops, 0.0) : -1;
@@ -1547,11 +1616,17 @@ bool resblock_cat(Ctx& c, size_t& wi, const LevelBufs& lb, const float* a, int C
   const ConvW& c1 = c.u->convs[wi++];
   const ConvW& c2 = c.u->convs[wi++];
   const ConvW& sk = c.u->convs[wi++];
+  // the shortcut folds into conv2's K loop when both run on the tensor cores
+  const bool fold = tc_path<TA>(c2, lb.H) && tc_path<TA>(sk, lb.H);
   const bool s2 = conv_run<TA>(c, c1, lb.T1, false, nullptr, (float*)lb.T2, lb.H, sp ? lb.T1lo : nullptr, lb.bT2);
-  conv_run<TA>(c, sk, lb.T4, false, nullptr, (float*)lb.T3, lb.H, sp ? lb.T4lo : nullptr);
+  if (!fold) conv_run<TA>(c, sk, lb.T4, false, nullptr, (float*)lb.T3, lb.H, sp ? lb.T4lo : nullptr);
   gn<TA>(c, (const float*)lb.T2, lb.H, cout, lb.T1, true, nullptr, sp ? lb.T1lo : nullptr, nullptr,
          s2 ? lb.bT2 : nullptr);
-  *y_stats = conv_run<TA>(c, c2, lb.T1, false, (const float*)lb.T3, Y, lb.H, sp ? lb.T1lo : nullptr, bsY);
+  if (fold)
+    *y_stats = conv_run<TA>(c, c2, lb.T1, false, nullptr, Y, lb.H, sp ? lb.T1lo : nullptr, bsY, &sk, lb.T4,
+                            sp ? lb.T4lo : nullptr);
+  else
+    *y_stats = conv_run<TA>(c, c2, lb.T1, false, (const float*)lb.T3, Y, lb.H, sp ? lb.T1lo : nullptr, bsY);
   return true;
 }
 
@@ -1569,14 +1644,19 @@ bool resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
   gn<TA>(c, X, b.H, cin, b.T1, true, need_copy ? b.T4 : nullptr, sp ? b.T1lo : nullptr,
          sp && need_copy ? b.T4lo : nullptr, bsX);
   const bool s2 = conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H, sp ? b.T1lo : nullptr, b.bT2);
+  // the shortcut folds into conv2's K loop when both run on the tensor cores
+  const bool fold = need_copy && tc_path<TA>(c2, b.H) && tc_path<TA>(*sk, b.H);
   const float* res = X;
-  if (sk) {
+  if (sk && !fold) {
     if (need_copy) conv_run<TA>(c, *sk, b.T4, false, nullptr, (float*)b.T3, b.H, sp ? b.T4lo : nullptr);
     else conv_run<TA>(c, *sk, X, true, nullptr, (float*)b.T3, b.H);
     res = (const float*)b.T3;
   }
   gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true, nullptr, sp ? b.T1lo : nullptr, nullptr,
          s2 ? b.bT2 : nullptr);
+  if (fold)
+    return conv_run<TA>(c, c2, b.T1, false, nullptr, Y, b.H, sp ? b.T1lo : nullptr, bsY, sk, b.T4,
+                        sp ? b.T4lo : nullptr);
   return conv_run<TA>(c, c2, b.T1, false, res, Y, b.H, sp ? b.T1lo : nullptr, bsY);
 }
 
@@ -1678,6 +1758,7 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
   }
   if (n <= 0) return true;
   if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err);
+  if (u->precision == 4) return forward_t<tf32>(u, x_in, n, F, st, err);
   return forward_t<float>(u, x_in, n, F, st, err);
 }
 

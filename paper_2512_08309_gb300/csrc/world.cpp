@@ -782,7 +782,8 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
   *out = nullptr;
   if (!stack || !opts || stack->n_levels < 1 || stack->n_levels > 2 || !stack->level) return IDF_EINVAL;
   if (opts->precision == IDF_FP8_E4M3) return IDF_EUNSUPPORTED;
-  if (opts->precision != IDF_FP32 && opts->precision != IDF_BF16 && opts->precision != IDF_BF16X3)
+  if (opts->precision != IDF_FP32 && opts->precision != IDF_BF16 && opts->precision != IDF_BF16X3 &&
+      opts->precision != IDF_TF32)
     return IDF_EINVAL;
   if (!(stack->blend_eps > 0) || !(stack->blend_eps <= 1)) return IDF_EINVAL;
   if (stack->laplacian) {

@@ -23,10 +23,10 @@ def case():
     return idf, st, wts, rect, ref
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16x3", 2e-2)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16x3", 2e-2), ("tf32", 2e-2)])
 def test_two_level_full_width(case, precision, tol):
-    # FP32 and the compensated BF16 path (IDF_BF16X3) against the stated
-    # bounds 1e-4 and 2e-2 sigma_out
+    # FP32, the compensated BF16 path (IDF_BF16X3) and TF32 operands against
+    # the stated bounds 1e-4 and 2e-2 sigma_out
     idf, st, wts, rect, ref = case
     W = idf.World(0, st, wts, precision=precision)
     got = W.query(*rect).astype(np.float64)

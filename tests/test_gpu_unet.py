@@ -75,3 +75,17 @@ def test_config2_unet_bf16x3(idf, li):
     err = np.max(np.abs(got - ref))
     print(f"level {li}: bf16x3 max {err / ref.std():.3e} sigma")
     assert err <= 1e-3 * ref.std()
+
+
+@pytest.mark.parametrize("li", [0, 1])
+def test_config2_unet_tf32(idf, li):
+    # Operands rounded to tf32 (11 significant bits, unit roundoff 2^-11,
+    # 8x finer than bfloat16's 2^-8) with one tensor-core product each: the
+    # error of the plain bfloat16 path above (~0.8% rms, ~4% max of a
+    # window) scaled down by 8
+    got, ref = run(idf, synth.config2_stack(), li, "tf32", 2, seed=li)
+    d = got - ref
+    rms = float(np.sqrt(np.mean(d * d)))
+    print(f"level {li}: tf32 rms {rms / ref.std():.3e} sigma, max {np.max(np.abs(d)) / ref.std():.3e} sigma")
+    assert rms <= 2.5e-3 * ref.std()
+    assert np.max(np.abs(d)) <= 1e-2 * ref.std()
