@@ -211,12 +211,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Persistent kernel: CTA c handles tiles c, c + gridDim.x, ... (channel tiles
-// of the same pixel tile are adjacent, so they share the activation tile in
-// L2).  The shared-memory ring of STAGES stages runs across tile boundaries;
-// two TMEM accumulators (2 x BN columns) let the epilogue of one tile overlap
-// the main loop of the next.
-template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32>
+// Persistent kernel: CTA c handles work units c, c + gridDim.x, ...  A unit
+// is MT consecutive 128-pixel M tiles of one window (MT = 1 or 2) times one
+// BN-channel N tile; with MT = 2 the two M tiles share every staged weight
+// tile (twice the MMA work per staged byte) and accumulate into two TMEM
+// tiles.  Channel tiles of the same pixels are adjacent units, so they share
+// the activations in L2.  The shared-memory ring of STAGES stages runs
+// across unit boundaries; two TMEM accumulator sets (2 x MT x BN columns)
+// let the epilogue of one unit overlap the main loop of the next.
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmA_lo,
@@ -227,16 +230,19 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                                          const __grid_constant__ CUtensorMap tmB2_lo,
                                                          TcParams p) {
   // DXR (3x3 convs on 128-pixel rows): a stage holds one kernel row dy: a
-  // 130-pixel activation box (halo columns zero-filled) read by the three
-  // horizontal taps at row offsets 0, 1, 2, and the three taps' weights.
-  constexpr int A_BOX = DXR ? (BM + 2) * 128 : BM * 128;    // bytes TMA writes
-  constexpr int A_BYTES = DXR ? 17 * 1024 : BM * 128;       // region, 1024-aligned
+  // 130-pixel activation box per image row (halo columns zero-filled; MT
+  // rows in one box) read by the three horizontal taps at row offsets 0, 1,
+  // 2, and the three taps' weights.
+  constexpr int A_ROW = DXR ? (BM + 2) * 128 : BM * 128;    // bytes of one M tile's rows
+  constexpr int A_BOX = A_ROW * MT;                         // bytes TMA writes
+  constexpr int A_BYTES = (A_BOX + 1023) / 1024 * 1024;     // region, 1024-aligned
   constexpr int B_BYTES = BN * 128;
   constexpr int NB = DXR ? 3 : 1;                           // weight tiles per stage
   constexpr int NP = SPLIT ? 2 : 1;                         // hi (and lo) parts per operand
   constexpr int STAGE_BYTES = NP * (A_BYTES + NB * B_BYTES);
   constexpr int TX_BYTES = NP * (A_BOX + NB * B_BYTES);
-  constexpr int TX2_BYTES = NP * (BM * 128 + B_BYTES);      // a folded 1x1 stage
+  constexpr int TX2_BYTES = NP * (BM * 128 * MT + B_BYTES); // a folded 1x1 stage
+  constexpr uint32_t ACC_COLS = MT * BN;                    // TMEM columns of one accumulator set
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t HW = (int64_t)p.H * p.W;
   const int pad = p.ks / 2;
-  const int n_tiles = p.m_tiles * p.n_tiles;
+  const int n_units = p.m_tiles / MT * p.n_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
-                 "r"(2 * BN)
+                 "r"(2 * ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -306,9 +312,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
       for (int s = 0; s < STAGES; ++s) last_issue[s] = -1;
       uint32_t it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t m0 = (int64_t)(tile / p.n_tiles) * BM;
-        const int n0 = (tile % p.n_tiles) * BN;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const int64_t m0 = (int64_t)(u / p.n_tiles) * (BM * MT);
+        const int n0 = (u % p.n_tiles) * BN;
         const int win = (int)(m0 / HW);
         const int y0 = (int)((m0 % HW) / p.W);
         for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           uint8_t* a = smem + (size_t)s * STAGE_BYTES;
           uint8_t* b = a + NP * A_BYTES;
           if (kk >= p.n_iter1) {
-            // folded 1x1 operand: the tile's own pixels, 64 channels
+            // folded 1x1 operand: the unit's own pixels, kch channels
             const int kc = kk - p.n_iter1;
             mbar_expect_tx(&full_bar[s], TX2_BYTES);
             tma_load_4d(a, &tmA2, &full_bar[s], kc * p.kch, 0, y0, win);
@@ -338,7 +344,8 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             for (int t = 0; t < 3; ++t) {
               tma_load_2d(b + t * B_BYTES, &tmB, &full_bar[s], kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
               if (SPLIT)
-                tma_load_2d(b + (3 + t) * B_BYTES, &tmB_lo, &full_bar[s], kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
+                tma_load_2d(b + (3 + t) * B_BYTES, &tmB_lo, &full_bar[s], kc * p.kch,
+                            (dyi * 3 + t) * p.Cout + n0);
             }
           } else {
             mbar_expect_tx(&full_bar[s], TX_BYTES);
@@ -366,11 +373,11 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
       constexpr uint32_t idesc = idesc_mma(BM, BN, TF32);
       uint32_t it = 0, acc = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++acc) {
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++acc) {
         const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
         if (!wait_bar(&acce_bar[buf], aph ^ 1u, abort_flag, p.status, true)) break;
         fence_after();
-        const uint32_t d = tmem + buf * BN;
+        const uint32_t d = tmem + buf * ACC_COLS;
         for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -382,13 +389,18 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
           const uint32_t b = a + NP * A_BYTES;
           if (kk >= p.n_iter1) {
-            // folded 1x1 operand (never the first K step of a tile)
+            // folded 1x1 operand (never the first K step of a unit); its M
+            // tiles are whole 128-pixel blocks of the box
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              mma_step<TF32>(d, umma_desc(a + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
-              if (SPLIT) {
-                mma_step<TF32>(d, umma_desc(a + A_BYTES + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
-                mma_step<TF32>(d, umma_desc(a + 32 * k), umma_desc(b + NB * B_BYTES + 32 * k), idesc, 1u);
+            for (int i = 0; i < MT; ++i) {
+              const uint32_t ai = a + i * BM * 128, di = d + i * BN;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                mma_step<TF32>(di, umma_desc(ai + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
+                if (SPLIT) {
+                  mma_step<TF32>(di, umma_desc(ai + A_BYTES + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
+                  mma_step<TF32>(di, umma_desc(ai + 32 * k), umma_desc(b + NB * B_BYTES + 32 * k), idesc, 1u);
+                }
               }
             }
             mma_commit(&empty_bar[s]);
@@ -396,16 +408,20 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           }
 #pragma unroll
           for (int t = 0; t < NB; ++t) {
-            // DXR: horizontal tap t reads the staged rows starting at row t
-            const uint32_t at = a + (DXR ? 128 * t : 0);
             const uint32_t bt = b + B_BYTES * t;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              mma_step<TF32>(d, umma_desc(at + 32 * k), umma_desc(bt + 32 * k), idesc,
-                       (kk > 0 || t > 0 || k > 0) ? 1u : 0u);
-              if (SPLIT) {
-                mma_step<TF32>(d, umma_desc(at + A_BYTES + 32 * k), umma_desc(bt + 32 * k), idesc, 1u);
-                mma_step<TF32>(d, umma_desc(at + 32 * k), umma_desc(bt + NB * B_BYTES + 32 * k), idesc, 1u);
+            for (int i = 0; i < MT; ++i) {
+              // M tile i reads its own rows of the box; DXR: horizontal tap t
+              // starts t rows further
+              const uint32_t at = a + i * A_ROW + (DXR ? 128 * t : 0), di = d + i * BN;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                mma_step<TF32>(di, umma_desc(at + 32 * k), umma_desc(bt + 32 * k), idesc,
+                               (kk > 0 || t > 0 || k > 0) ? 1u : 0u);
+                if (SPLIT) {
+                  mma_step<TF32>(di, umma_desc(at + A_BYTES + 32 * k), umma_desc(bt + 32 * k), idesc, 1u);
+                  mma_step<TF32>(di, umma_desc(at + 32 * k), umma_desc(bt + NB * B_BYTES + 32 * k), idesc, 1u);
+                }
               }
             }
           }
@@ -422,57 +438,78 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     const int q = warp & 3;
     const int row = q * 32 + lane;
     uint32_t acc = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++acc) {
+    // The residual is read one 32-column chunk ahead (the next unit's first
+    // chunk after a unit's last), so its memory latency overlaps the work on
+    // the current chunk.  Each thread still reads every residual element
+    // before it writes the same output element.
+    float4 nx[8];
+    auto load_res = [&](int uu, int i, int c) {
+      const int64_t mm = (int64_t)(uu / p.n_tiles) * (BM * MT) + i * BM + row;
+      const float4* src = reinterpret_cast<const float4*>(p.res + mm * p.Cout + (uu % p.n_tiles) * BN + c);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) nx[j] = src[j];
+    };
+    if (p.res && (int)blockIdx.x < n_units) load_res(blockIdx.x, 0, 0);
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++acc) {
       const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
       if (!wait_bar(&accf_bar[buf], aph, abort_flag, p.status, true)) break;
       fence_after();
-      const int64_t m = (int64_t)(tile / p.n_tiles) * BM + row;
-      const int n0 = (tile % p.n_tiles) * BN;
+      const int n0 = (u % p.n_tiles) * BN;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + buf * BN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-        float* yp = p.y + m * p.Cout + n0 + c0;
-        const float* rp = p.res ? p.res + m * p.Cout + n0 + c0 : nullptr;
+      for (int i = 0; i < MT; ++i) {
+        const int64_t m = (int64_t)(u / p.n_tiles) * (BM * MT) + i * BM + row;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          float4 rv[8];
+          if (p.res) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-          if (rp) {
-            const float4 rv = reinterpret_cast<const float4*>(rp)[j];
-            v.x += rv.x; v.y += rv.y; v.z += rv.z; v.w += rv.w;
+            for (int j = 0; j < 8; ++j) rv[j] = nx[j];
+            if (c0 + 32 < BN) load_res(u, i, c0 + 32);
+            else if (i + 1 < MT) load_res(u, i + 1, 0);
+            else if (u + (int)gridDim.x < n_units) load_res(u + gridDim.x, 0, 0);
           }
-          reinterpret_cast<float4*>(yp)[j] = v;
-          r[4 * j] = __float_as_uint(v.x);
-          r[4 * j + 1] = __float_as_uint(v.y);
-          r[4 * j + 2] = __float_as_uint(v.z);
-          r[4 * j + 3] = __float_as_uint(v.w);
-        }
-        if (p.bstats) {
+          uint32_t r[32];
+          tmem_ld32(tmem + buf * ACC_COLS + i * BN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+          float* yp = p.y + m * p.Cout + n0 + c0;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float sum = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) sum += __uint_as_float(r[16 * h + k]);
-            float mu = sum * 0.0625f, m2 = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const float dv = __uint_as_float(r[16 * h + k]) - mu;
-              m2 = fmaf(dv, dv, m2);
+          for (int j = 0; j < 8; ++j) {
+            float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                   __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+            if (p.res) {
+              v.x += rv[j].x; v.y += rv[j].y; v.z += rv[j].z; v.w += rv[j].w;
             }
-            // merge equal-count partials of lanes l and l ^ o (n values each)
-            float half_n = 16.0f * 0.5f;
+            reinterpret_cast<float4*>(yp)[j] = v;
+            r[4 * j] = __float_as_uint(v.x);
+            r[4 * j + 1] = __float_as_uint(v.y);
+            r[4 * j + 2] = __float_as_uint(v.z);
+            r[4 * j + 3] = __float_as_uint(v.w);
+          }
+          if (p.bstats) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const float mo = __shfl_xor_sync(0xffffffffu, mu, o);
-              const float m2o = __shfl_xor_sync(0xffffffffu, m2, o);
-              const float dm = mo - mu;
-              m2 = (m2 + m2o) + dm * dm * half_n;
-              mu = (mu + mo) * 0.5f;
-              half_n *= 2.0f;
+            for (int h = 0; h < 2; ++h) {
+              float sum = 0.0f;
+#pragma unroll
+              for (int k = 0; k < 16; ++k) sum += __uint_as_float(r[16 * h + k]);
+              float mu = sum * 0.0625f, m2 = 0.0f;
+#pragma unroll
+              for (int k = 0; k < 16; ++k) {
+                const float dv = __uint_as_float(r[16 * h + k]) - mu;
+                m2 = fmaf(dv, dv, m2);
+              }
+              // merge equal-count partials of lanes l and l ^ o (n values each)
+              float half_n = 16.0f * 0.5f;
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const float mo = __shfl_xor_sync(0xffffffffu, mu, o);
+                const float m2o = __shfl_xor_sync(0xffffffffu, m2, o);
+                const float dm = mo - mu;
+                m2 = (m2 + m2o) + dm * dm * half_n;
+                mu = (mu + mo) * 0.5f;
+                half_n *= 2.0f;
+              }
+              if (lane == 0)
+                p.bstats[(m >> 5) * (p.Cout >> 4) + ((n0 + c0) >> 4) + h] = make_float2(mu, m2);
             }
-            if (lane == 0)
-              p.bstats[(m >> 5) * (p.Cout >> 4) + ((n0 + c0) >> 4) + h] = make_float2(mu, m2);
           }
         }
       }
@@ -485,7 +522,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
   if (warp == 1) {
     __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS)
                  : "memory");
   }
 }
@@ -518,22 +555,28 @@ struct Maps {
   CUtensorMap a2, b2, a2lo, b2lo;  // folded 1x1 operand (copies of the above when absent)
 };
 
-template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32 = false>
+// Shared memory of one stage, as the kernel lays it out.
+constexpr int stage_bytes(int BN, bool SPLIT, bool DXR, int MT) {
+  return (SPLIT ? 2 : 1) * ((((DXR ? (BM + 2) * 128 : BM * 128) * MT + 1023) / 1024 * 1024) + (DXR ? 3 : 1) * BN * 128);
+}
+
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT>
 bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err) {
-  const size_t smem = (size_t)STAGES * (SPLIT ? 2 : 1) * ((DXR ? 17 * 1024 : BM * 128) + (DXR ? 3 : 1) * BN * 128) + 1024;
+  constexpr size_t smem = (size_t)STAGES * stage_bytes(BN, SPLIT, DXR, MT) + 1024;
+  static_assert(smem <= 227 * 1024, "stages exceed the shared memory of a CTA");
+  static_assert(2 * MT * BN <= 512, "accumulators exceed tensor memory");
   static bool attr = false;
+  auto kern = conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32, MT>;
   if (!attr) {
-    if (cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       *err = "cudaFuncSetAttribute failed";
       return false;
     }
     attr = true;
   }
-  const int tiles = p.m_tiles * p.n_tiles;
-  const int grid = tiles < sm_count() ? tiles : sm_count();
-  conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32><<<grid, 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo,
-                                                                    m.b2lo, p);
+  const int units = p.m_tiles / MT * p.n_tiles;
+  const int grid = units < sm_count() ? units : sm_count();
+  kern<<<grid, 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo, m.b2lo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -607,7 +650,10 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  const int abw = dxr ? W + 2 : W, abh = dxr ? 1 : 128 / W;
+  // two M tiles per work unit when every window holds an even number of
+  // them, except for split 64-channel stages (too large twice over)
+  const int mt = (((int64_t)H * W / BM) % 2 == 0 && !(split && BN == 64) && BN <= 128) ? 2 : 1;
+  const int abw = dxr ? W + 2 : W, abh = dxr ? mt : mt * 128 / W;
   if (!encA(&m.a, x, Cin, abw, abh) || !encB(&m.b, w, Cin, ks * ks)) {
     *err = "tensor map (activations or weights) encode failed";
     return false;
@@ -621,11 +667,11 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
     m.blo = m.b;
   }
   if (fold) {
-    if (!encA(&m.a2, x2, Cin2, W, 128 / W) || !encB(&m.b2, w2, Cin2, 1)) {
+    if (!encA(&m.a2, x2, Cin2, W, mt * 128 / W) || !encB(&m.b2, w2, Cin2, 1)) {
       *err = "tensor map (folded operand) encode failed";
       return false;
     }
-    if (split && (!encA(&m.a2lo, x2_lo, Cin2, W, 128 / W) || !encB(&m.b2lo, w2_lo, Cin2, 1))) {
+    if (split && (!encA(&m.a2lo, x2_lo, Cin2, W, mt * 128 / W) || !encB(&m.b2lo, w2_lo, Cin2, 1))) {
       *err = "tensor map (folded operand low parts) encode failed";
       return false;
     }
@@ -654,25 +700,37 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   p.n_iter = p.n_iter1 + (fold ? Cin2 / kch : 0);
   p.m_tiles = (int)((int64_t)n * H * W / BM);
   p.n_tiles = Cout / BN;
-  // stages: about 192 KB of shared memory per CTA, one CTA per SM
-  if (tf32) {
-    switch (BN) {
-      case 64: return dxr ? launch<64, 5, false, true, true>(m, p, st, err)
-                          : launch<64, 8, false, false, true>(m, p, st, err);
-      case 128: return launch<128, 6, false, false, true>(m, p, st, err);
-      case 256: return launch<256, 4, false, false, true>(m, p, st, err);
+  // stages: about 170-200 KB of shared memory per CTA, one CTA per SM
+  if (!split) {
+    // bfloat16 or tf32 operands: the same stage bytes
+#define IDF_TC_PLAIN(TF)                                                                      \
+    if (mt == 2) {                                                                            \
+      switch (BN) {                                                                           \
+        case 64: return dxr ? launch<64, 3, false, true, TF, 2>(m, p, st, err)                \
+                            : launch<64, 5, false, false, TF, 2>(m, p, st, err);              \
+        case 128: return launch<128, 4, false, false, TF, 2>(m, p, st, err);                  \
+      }                                                                                       \
+    } else {                                                                                  \
+      switch (BN) {                                                                           \
+        case 64: return dxr ? launch<64, 5, false, true, TF, 1>(m, p, st, err)                \
+                            : launch<64, 8, false, false, TF, 1>(m, p, st, err);              \
+        case 128: return launch<128, 6, false, false, TF, 1>(m, p, st, err);                  \
+        case 256: return launch<256, 4, false, false, TF, 1>(m, p, st, err);                  \
+      }                                                                                       \
     }
-  } else if (!split) {
-    switch (BN) {
-      case 64: return dxr ? launch<64, 5, false, true>(m, p, st, err) : launch<64, 8, false, false>(m, p, st, err);
-      case 128: return launch<128, 6, false, false>(m, p, st, err);
-      case 256: return launch<256, 4, false, false>(m, p, st, err);
+    if (tf32) {
+      IDF_TC_PLAIN(true)
+    } else {
+      IDF_TC_PLAIN(false)
     }
+#undef IDF_TC_PLAIN
   } else {
     switch (BN) {
-      case 64: return dxr ? launch<64, 2, true, true>(m, p, st, err) : launch<64, 4, true, false>(m, p, st, err);
-      case 128: return launch<128, 3, true, false>(m, p, st, err);
-      case 256: return launch<256, 2, true, false>(m, p, st, err);
+      case 64: return dxr ? launch<64, 2, true, true, false, 1>(m, p, st, err)
+                          : launch<64, 4, true, false, false, 1>(m, p, st, err);
+      case 128: return mt == 2 ? launch<128, 2, true, false, false, 2>(m, p, st, err)
+                               : launch<128, 3, true, false, false, 1>(m, p, st, err);
+      case 256: return launch<256, 2, true, false, false, 1>(m, p, st, err);
     }
   }
   *err = "unsupported N tile";
