@@ -56,7 +56,7 @@ typedef enum {
  * path with each operand split as hi + lo (both bfloat16) and the products
  * hi*hi + lo*hi + hi*lo accumulated, which compensates the rounding of both
  * operands at three times the tensor work.  IDF_TF32: operands rounded to
- * tf32 (10 explicit mantissa bits, round to nearest even) and one tensor-core
+ * tf32 (10 explicit mantissa bits, round to nearest, ties away) and one tensor-core
  * product per multiply-add (kind::tf32, half the bf16 rate), float32
  * accumulation and residual stream.  IDF_FP8_E4M3 is not built yet. */
 typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2, IDF_BF16X3 = 3, IDF_TF32 = 4 } idf_precision;

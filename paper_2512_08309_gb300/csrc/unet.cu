@@ -44,13 +44,23 @@ struct tf32 {
   float f;
 };
 
-// Round to nearest, ties to even, at mantissa bit 13 (finite values).
-__host__ __device__ __forceinline__ uint32_t tf32_rn_bits(uint32_t u) {
+// Round to nearest at mantissa bit 13, ties away from zero (the rounding of
+// cvt.rna.tf32.f32, which the device uses; the host rounds the weights the
+// same way).  Finite values only.
+inline uint32_t tf32_rna_bits_host(uint32_t u) {
   if ((u & 0x7f800000u) == 0x7f800000u) return u;
-  u += 0xfffu + ((u >> 13) & 1u);
-  return u & 0xffffe000u;
+  return (u + 0x1000u) & 0xffffe000u;
 }
-__device__ __forceinline__ float tf32_rn(float v) { return __uint_as_float(tf32_rn_bits(__float_as_uint(v))); }
+__device__ __forceinline__ float tf32_rn(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// SiLU z / (1 + e^-z) with the fast exponential and division (a few ulp;
+// for very negative z the denominator overflows and the result is 0, the
+// limit of z e^z).
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 template <typename T> __device__ __forceinline__ float ld(const T* p);
 template <> __device__ __forceinline__ float ld<float>(const float* p) { return *p; }
@@ -225,7 +235,7 @@ __global__ void gn_apply_kernel(const Tin* __restrict__ x, const float2* __restr
     const float2 ms = stats[b * G + c / Cg];
     const float xv = ld<Tin>(x + i);
     float v = (xv - ms.x) * ms.y;
-    if (SILU) v = v / (1.0f + expf(-v));
+    if (SILU) v = silu_fast(v);
     st<Tout>(y + i, v);
     if (copy) st<Tout>(copy + i, xv);
     if (ylo) st<Tout>(ylo + i, v - ld<Tout>(y + i));
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       float z = (xv[j] - ms.x) * ms.y;
-      if (SILU) z = z / (1.0f + expf(-z));
+      if (SILU) z = silu_fast(z);
       v[j] = z;
     }
     Pack8<TA>::store(y + (int64_t)u * 8, v);
@@ -546,7 +556,7 @@ __global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const fl
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       float z = (xv[j] - ms.x) * ms.y;
-      if (SILU) z = z / (1.0f + expf(-z));
+      if (SILU) z = silu_fast(z);
       v[j] = z;
     }
     Pack8<TA>::store(y + (int64_t)u * 8, v);
@@ -841,6 +851,88 @@ __global__ void __launch_bounds__(256) conv_out_tile2_kernel(const TA* __restric
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const float wv = ws[tap * Cin + c0 + ch];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) acc[i] = fmaf(v[i + tap / 3][tap % 3], wv, acc[i]);
+      }
+    }
+  }
+  float* yb = y + (b * H + r0) * W;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) yb[(rr + i) * W + col] = acc[i];
+}
+
+// Output head, fused: F = conv3x3(silu(gn(x))) with one output channel, x
+// float32 NHWC (C channels in G groups, statistics given per window and
+// group).  A CTA owns THIN_R rows of one window; CH channels at a time, the
+// (THIN_R + 2) x (W + 2) neighbourhood is normalised into shared memory
+// (zero outside the window: the padding applies after the activation) and
+// thread (column, row block) accumulates RPT outputs.  The normalised
+// operand never goes through memory.  Each pass issues all of its global
+// loads before using any of them.
+template <int RPT>
+__global__ void __launch_bounds__(256) gn_silu_conv_out_kernel(const float* __restrict__ x,
+                                                               const float2* __restrict__ stats,
+                                                               const float* __restrict__ wk,
+                                                               float* __restrict__ y, int H, int W, int C,
+                                                               int G) {
+  extern __shared__ float sm[];
+  constexpr int R = THIN_R, CH = 8, PER = 6;  // PER x 256 >= (R + 2) x (W + 2) for W <= 128
+  const int W2 = W + 2;
+  const int RW = (R + 2) * W2;
+  float* xs = sm;            // [CH][R+2][W+2]
+  float* ws = sm + CH * RW;  // [9][C]
+  const int r0 = blockIdx.x * R;
+  const int64_t b = blockIdx.y;
+  const float* xb = x + b * H * W * C;
+  const int Cg = C / G;
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) ws[i] = wk[i];
+  const int col = threadIdx.x % W, rr = (threadIdx.x / W) * RPT;
+  float acc[RPT];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) acc[j] = 0.0f;
+  for (int c0 = 0; c0 < C; c0 += CH) {
+    const float2 ms = stats[b * G + c0 / Cg];  // CH channels lie in one group
+    float4 va[PER], vb[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int p = threadIdx.x + k * 256;
+      va[k] = vb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int pr = p / W2, pc = p % W2;
+      const int gy = r0 + pr - 1, gx = pc - 1;
+      if (p < RW && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        const float4* src = reinterpret_cast<const float4*>(xb + ((int64_t)gy * W + gx) * C + c0);
+        va[k] = src[0];
+        vb[k] = src[1];
+      }
+    }
+    __syncthreads();  // the previous pass's readers are done with xs
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int p = threadIdx.x + k * 256;
+      if (p < RW) {
+        const int pr = p / W2, pc = p % W2;
+        const int gy = r0 + pr - 1, gx = pc - 1;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const float v[8] = {va[k].x, va[k].y, va[k].z, va[k].w, vb[k].x, vb[k].y, vb[k].z, vb[k].w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float z = silu_fast((v[j] - ms.x) * ms.y);
+          xs[j * RW + p] = in ? z : 0.0f;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ch = 0; ch < CH; ++ch) {
+      const float* xc = xs + ch * RW + rr * W2 + col;
+      float v[RPT + 2][3];
+#pragma unroll
+      for (int i = 0; i < RPT + 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) v[i][j] = xc[i * W2 + j];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const float wv = ws[tap * C + c0 + ch];
 #pragma unroll
         for (int i = 0; i < RPT; ++i) acc[i] = fmaf(v[i + tap / 3][tap % 3], wv, acc[i]);
       }
@@ -1312,7 +1404,7 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
             uint32_t u;
             const float v = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
             std::memcpy(&u, &v, 4);
-            u = tf32_rn_bits(u);
+            u = tf32_rna_bits_host(u);
             std::memcpy(&pt[((size_t)t * c.cout + o) * c.cin + ci], &u, 4);
           }
       if (!ck(cudaMalloc(&c.wtf, pt.size() * 4), err, "cudaMalloc tf32 weights")) { unet_destroy(u); return nullptr; }
@@ -1497,6 +1589,20 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
   return false;
 }
 
+// The apply pass of GroupNorm with the statistics in c.u->stats, 8 channels
+// (one group's share) per thread.
+template <typename TA>
+void gn_apply_launch(Ctx& c, const float* x, int HW, int C, bool silu, void* y, void* copy, void* ylo,
+                     void* copylo) {
+  const int G = c.u->d.groups;
+  const int64_t units = (int64_t)c.n * HW * (C / 8);
+  const int upw = HW * (C / 8);
+  if (silu)
+    gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+  else
+    gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+}
+
 // y (TA) = silu(gn(x)) or gn(x); copy (TA, optional) = x
 // With bs (block partials of x from the convolution that wrote it) the
 // statistics come from those instead of a pass over x.
@@ -1519,11 +1625,7 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
   if (blk) {
     const BlkSrc src{nullptr, bs, 0, C, 0, HW / 32};
     gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(src, c.n, G, c.u->stats);
-    const int upw = HW * (C / 8);
-    if (silu)
-      gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
-    else
-      gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    gn_apply_launch<TA>(c, x, HW, C, silu, y, copy, ylo, copylo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches += 2;
     return;
@@ -1539,11 +1641,7 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
     }
     gn_partial_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(x, HW, C, G, chunk_px, c.u->gnpart);
     gn_finalize_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
-    const int upw = HW * (C / 8);
-    if (silu)
-      gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
-    else
-      gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    gn_apply_launch<TA>(c, x, HW, C, silu, y, copy, ylo, copylo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches += 3;
     return;
@@ -1556,6 +1654,57 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
     gn_apply_kernel<float, TA, false><<<grid1d(nel, 256), 256, 0, c.st>>>(x, c.u->stats, nel, H * H, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
   if (c.u->prof) c.u->prof->end(pr, c.st);
   c.u->launches += 2;
+}
+
+// Output head F = conv3x3(silu(gn(x))) (one output channel) as one fused
+// pass over x after the statistics; returns false when the shape does not
+// fit the fused kernel (the caller then runs GroupNorm and the conv apart).
+bool out_head(Ctx& c, const float* x, int H, int C, const ConvW& w, float* F, const float2* bs) {
+  const int G = c.u->d.groups, Cg = C / G, HW = H * H, W = H;
+  if (!(w.ks == 3 && w.cout == 1 && w.cin == C && C % 8 == 0 && Cg % 8 == 0 && Cg / 4 <= 256 &&
+        H % THIN_R == 0 && (W == 128 || W == 64 || W == 32)))
+    return false;
+  if (!c.ok) return true;
+  const double nb = (double)c.n * HW * C;
+  const bool blk = bs && C % 16 == 0 && Cg % 16 == 0 && HW % 32 == 0;
+  int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, blk ? 0.0 : 4.0 * nb) : -1;
+  if (blk) {
+    const BlkSrc src{nullptr, bs, 0, C, 0, HW / 32};
+    gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(src, c.n, G, c.u->stats);
+    c.u->launches += 1;
+  } else {
+    const int Q = Cg / 4, P = 256 / Q;
+    int chunk_px = std::max(P, 8192 / Cg);
+    int chunks = (HW + chunk_px - 1) / chunk_px;
+    if (chunks > GN_MAX_CHUNKS) {
+      chunk_px = (HW + GN_MAX_CHUNKS - 1) / GN_MAX_CHUNKS;
+      chunks = (HW + chunk_px - 1) / chunk_px;
+    }
+    gn_partial_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(x, HW, C, G, chunk_px, c.u->gnpart);
+    gn_finalize_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
+    c.u->launches += 2;
+  }
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+  // the fused pass: float32 input read once (with its row halo), F written
+  pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, 2.0 * c.n * HW * 9.0 * C, nb * 4.0 + 4.0 * c.n * HW) : -1;
+  const size_t smem = ((size_t)8 * (THIN_R + 2) * (W + 2) + 9 * C) * sizeof(float);
+  const dim3 grid(H / THIN_R, c.n);
+  const int rpt = THIN_R * W / 256;
+  auto kern = rpt == 4 ? gn_silu_conv_out_kernel<4> : rpt == 2 ? gn_silu_conv_out_kernel<2> : gn_silu_conv_out_kernel<1>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid, 256, smem, c.st>>>(x, c.u->stats, w.w32, F, H, W, C, G);
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+  c.u->launches++;
+  return true;
+}
+
+// The apply pass over the virtual concat (with SiLU), 8 channels per thread.
+template <typename TA>
+void gn_apply_cat_launch(Ctx& c, const CatSrc& src, void* y, void* copy, void* ylo, void* copylo) {
+  const int G = c.u->d.groups, C = src.Ca + src.Cb, HW = src.H * src.H;
+  const int64_t units = (int64_t)c.n * HW * (C / 8);
+  gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
+                                                                       (TA*)copy, (TA*)ylo, (TA*)copylo);
 }
 
 // GroupNorm + SiLU of the virtual concat [up2(a), b]; writes the operand y and
@@ -1579,8 +1728,7 @@ bool gn_cat(Ctx& c, const float* a, int Ca, const float* b, int Cb, int H, void*
   if (blk) {
     const BlkSrc bsrc{bsa, bsb, Ca, Cb, HW / 128, HW / 32};
     gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(bsrc, c.n, G, c.u->stats);
-    gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
-                                                                         (TA*)copy, (TA*)ylo, (TA*)copylo);
+    gn_apply_cat_launch<TA>(c, src, y, copy, ylo, copylo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches += 2;
     return true;
@@ -1594,8 +1742,7 @@ bool gn_cat(Ctx& c, const float* a, int Ca, const float* b, int Cb, int H, void*
   }
   gn_partial_cat_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(src, G, chunk_px, c.u->gnpart);
   gn_finalize_cat_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(src, c.u->gnpart, c.n, chunks, G, c.u->stats);
-  gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
-                                                                       (TA*)copy, (TA*)ylo, (TA*)copylo);
+  gn_apply_cat_launch<TA>(c, src, y, copy, ylo, copylo);
   if (c.u->prof) c.u->prof->end(pr, c.st);
   c.u->launches += 3;
   return true;
@@ -1734,9 +1881,12 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     prev = d.ch[l];
   }
   LevelBufs& b0 = u->lv[0];
-  gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true, nullptr, u->split ? b0.T1lo : nullptr, nullptr,
-         m_st[0] ? b0.bM : nullptr);
-  conv_run<TA>(c, u->convs[wi++], b0.T1, false, nullptr, F, d.window, u->split ? b0.T1lo : nullptr);
+  const ConvW& wo = u->convs[wi++];
+  if (!out_head(c, (const float*)b0.M, b0.H, prev, wo, F, m_st[0] ? b0.bM : nullptr)) {
+    gn<TA>(c, (const float*)b0.M, b0.H, prev, b0.T1, true, nullptr, u->split ? b0.T1lo : nullptr, nullptr,
+           m_st[0] ? b0.bM : nullptr);
+    conv_run<TA>(c, wo, b0.T1, false, nullptr, F, d.window, u->split ? b0.T1lo : nullptr);
+  }
   if (c.ok) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
