@@ -202,6 +202,9 @@ struct TcParams {
   float2* bstats;  // null, or (mean, M2) per (32-pixel block, 16-channel slice)
   int* status;
   int H, W, Cout, ks, n_kc, n_iter;
+  int oy, ox;            // input offset of tap (0, 0): tap t reads (y + t / ks + oy, x + t % ks + ox)
+  int out_up, py, px;    // out_up: pixel (y, x) is stored at (2y + py, 2x + px) of a 2H x 2W output
+  int res_up;            // res_up: the residual of pixel (y, x) is element (y / 2, x / 2) of an H/2 x W/2 tensor
   int kch;               // input channels per K stage (64 bf16 or 32 tf32: 128 bytes)
   int n_iter1;           // K iterations of the main operand; the rest are the folded 1x1 operand
   int m_tiles, n_tiles;  // output tiles: 128-pixel rows x BN channels
@@ -262,7 +265,6 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t HW = (int64_t)p.H * p.W;
-  const int pad = p.ks / 2;
   const int n_units = p.m_tiles / MT * p.n_tiles;
 
   if (threadIdx.x == 0) {
@@ -339,8 +341,8 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           } else if (DXR) {
             mbar_expect_tx(&full_bar[s], TX_BYTES);
             const int dyi = kk / p.n_kc, kc = kk % p.n_kc;
-            tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, -1, y0 + dyi - 1, win);
-            if (SPLIT) tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * p.kch, -1, y0 + dyi - 1, win);
+            tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, p.ox, y0 + dyi + p.oy, win);
+            if (SPLIT) tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * p.kch, p.ox, y0 + dyi + p.oy, win);
             for (int t = 0; t < 3; ++t) {
               tma_load_2d(b + t * B_BYTES, &tmB, &full_bar[s], kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
               if (SPLIT)
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           } else {
             mbar_expect_tx(&full_bar[s], TX_BYTES);
             const int tap = kk / p.n_kc, kc = kk % p.n_kc;
-            const int dy = tap / p.ks - pad, dx = tap % p.ks - pad;
+            const int dy = tap / p.ks + p.oy, dx = tap % p.ks + p.ox;
             tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, dx, y0 + dy, win);
             tma_load_2d(b, &tmB, &full_bar[s], kc * p.kch, tap * p.Cout + n0);
             if (SPLIT) {
@@ -443,8 +445,15 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     // the current chunk.  Each thread still reads every residual element
     // before it writes the same output element.
     float4 nx[8];
+    // element index of pixel m's residual (same grid, or half resolution)
+    auto res_index = [&](int64_t m) -> int64_t {
+      if (!p.res_up) return m;
+      const int64_t w = m / HW, r = m % HW;
+      const int yy = (int)(r / p.W), xx = (int)(r % p.W);
+      return w * (HW / 4) + (int64_t)(yy >> 1) * (p.W >> 1) + (xx >> 1);
+    };
     auto load_res = [&](int uu, int i, int c) {
-      const int64_t mm = (int64_t)(uu / p.n_tiles) * (BM * MT) + i * BM + row;
+      const int64_t mm = res_index((int64_t)(uu / p.n_tiles) * (BM * MT) + i * BM + row);
       const float4* src = reinterpret_cast<const float4*>(p.res + mm * p.Cout + (uu % p.n_tiles) * BN + c);
 #pragma unroll
       for (int j = 0; j < 8; ++j) nx[j] = src[j];
@@ -470,7 +479,13 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
           }
           uint32_t r[32];
           tmem_ld32(tmem + buf * ACC_COLS + i * BN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-          float* yp = p.y + m * p.Cout + n0 + c0;
+          int64_t mo = m;
+          if (p.out_up) {
+            const int64_t w = m / HW, r = m % HW;
+            const int yy = (int)(r / p.W), xx = (int)(r % p.W);
+            mo = w * (4 * HW) + (int64_t)(2 * yy + p.py) * (2 * p.W) + (2 * xx + p.px);
+          }
+          float* yp = p.y + mo * p.Cout + n0 + c0;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
@@ -588,7 +603,7 @@ bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err)
 }  // namespace
 
 bool conv_tc_supported(int cin, int cout, int ks) {
-  return (ks == 1 || ks == 3) && cin >= 64 && cin % 64 == 0 && cout >= 64 && cout % 64 == 0 &&
+  return (ks == 1 || ks == 2 || ks == 3) && cin >= 64 && cin % 64 == 0 && cout >= 64 && cout % 64 == 0 &&
          (cout <= 256 || cout % 256 == 0);
 }
 
@@ -599,7 +614,7 @@ bool conv_tc_shape_ok(int H, int W) {
 bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void* w_lo, const float* res,
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
                      cudaStream_t st, std::string* err, const void* x2, const void* w2, const void* x2_lo,
-                     const void* w2_lo, int Cin2, bool tf32) {
+                     const void* w2_lo, int Cin2, bool tf32, const TcGeom* geom) {
   if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
     *err = "shape not supported by the tensor-core convolution";
     return false;
@@ -629,7 +644,7 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   }
   Maps m;
   // 3x3 convs on 128-pixel rows stage one 130-pixel box per kernel row
-  const bool dxr = ks == 3 && W == 128 && BN == 64;
+  const bool dxr = ks == 3 && W == 128 && BN == 64 && (!geom || (geom->oy == -1 && geom->ox == -1));
   // activations (n, H, W, C); box of kch channels x bw pixels x bh rows
   auto encA = [&](CUtensorMap* mp, const void* ptr, int C, int bw, int bh) {
     cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
@@ -694,6 +709,17 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   p.W = W;
   p.Cout = Cout;
   p.ks = ks;
+  const TcGeom g = geom ? *geom : TcGeom{};
+  p.oy = geom ? g.oy : -(ks / 2);
+  p.ox = geom ? g.ox : -(ks / 2);
+  p.out_up = g.out_up;
+  p.py = g.py;
+  p.px = g.px;
+  p.res_up = g.res_up;
+  if ((p.out_up && (bstats || res)) || (p.res_up && ((H | W) & 1))) {
+    *err = "unsupported combination of phase output, residual and statistics";
+    return false;
+  }
   p.kch = kch;
   p.n_kc = Cin / kch;
   p.n_iter1 = (dxr ? ks : ks * ks) * p.n_kc;

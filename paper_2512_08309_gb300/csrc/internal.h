@@ -185,8 +185,33 @@ int64_t unet_launches(const UNet* u);
 int* unet_status(const UNet* u);
 void unet_set_prof(UNet* u, Prof* p);
 
-// tcgen05 conv availability (compiled in conv_tc.cu)
+// tcgen05 conv (conv_tc.cu)
 bool conv_tc_supported(int cin, int cout, int ks);
+bool conv_tc_shape_ok(int H, int W);
+
+// Geometry options of a tensor-core convolution: the input offset of tap
+// (0, 0) (the default -ks/2 centres the kernel), a phase-scattered output
+// (pixel (y, x) of the H x W grid is stored at (2y + py, 2x + px) of a
+// 2H x 2W output: one phase of a convolution over a nearest-upsampled
+// input), and a half-resolution residual (pixel (y, x) adds element
+// (y/2, x/2) of an H/2 x W/2 tensor: a nearest-upsampled residual).
+struct TcGeom {
+  int oy = 0, ox = 0;
+  int out_up = 0, py = 0, px = 0;
+  int res_up = 0;
+};
+
+// y (float32 NHWC, Cout) = conv(x) over (tap, Cin) [+ the 1x1 conv of x2
+// over Cin2, folded into the same accumulator] [+ res], x / x2 in bfloat16
+// (with low parts for the compensated split) or tf32-rounded float32.  With
+// bstats the epilogue also writes GroupNorm block partials of y.  Returns
+// false with err set when the shape or combination is not supported or a
+// launch fails.
+bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void* w_lo, const float* res,
+                     float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
+                     cudaStream_t st, std::string* err, const void* x2 = nullptr, const void* w2 = nullptr,
+                     const void* x2_lo = nullptr, const void* w2_lo = nullptr, int Cin2 = 0, bool tf32 = false,
+                     const TcGeom* geom = nullptr);
 
 // float32 building blocks (unet.cu), NHWC, square images
 void launch_conv_f32(const float* x, const float* wk, const float* res, float* y, int n, int H, int W,

@@ -422,19 +422,22 @@ template <> struct Pack8<bf16> {
   }
 };
 
+// x holds C channels of a tensor whose groups are Cg channels wide; its
+// channel c is channel c + coff of that tensor (coff > 0: the second part of
+// a concat normalised with the concat's statistics).
 template <typename TA, bool SILU>
 __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict__ x,
                                                         const float2* __restrict__ stats,
                                                         int n_units, int units_per_win, int C,
-                                                        int G, TA* __restrict__ y,
+                                                        int G, int Cg, int coff, TA* __restrict__ y,
                                                         TA* __restrict__ copy,
                                                         TA* __restrict__ ylo,
                                                         TA* __restrict__ copylo) {
-  const int C8 = C / 8, Cg = C / G;
+  const int C8 = C / 8;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
     const int b = u / units_per_win;
     const int c0 = (u % C8) * 8;
-    const float2 ms = stats[b * G + c0 / Cg];
+    const float2 ms = stats[b * G + (c0 + coff) / Cg];
     const float4* src = reinterpret_cast<const float4*>(x + (int64_t)u * 8);
     const float4 a = src[0], bq = src[1];
     float xv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
@@ -1199,11 +1202,6 @@ __global__ void attention_kernel(const float* __restrict__ qkv, int Tn, int C, i
 }
 
 // ------------------------------------------------------------ engine
-bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void* w_lo, const float* res,
-                     float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
-                     cudaStream_t st, std::string* err, const void* x2 = nullptr, const void* w2 = nullptr,
-                     const void* x2_lo = nullptr, const void* w2_lo = nullptr, int Cin2 = 0, bool tf32 = false);
-bool conv_tc_shape_ok(int H, int W);
 
 struct ConvW {
   int cin = 0, cout = 0, ks = 0;
@@ -1239,12 +1237,23 @@ struct LevelBufs {
   float2* bCAT = nullptr;
 };
 
+// Tensor-core weights of the half-resolution form of one decoder ResBlock
+// (see make_dec_weights).
+struct DecW {
+  ConvW w1s;     // conv1 over the skip's channels, 3x3
+  ConvW w1p[4];  // conv1 over the upsampled channels: phase (py, px) -> 2x2 at half resolution
+  ConvW wska;    // shortcut over the upsampled channels, 1x1 at half resolution
+  ConvW wsks;    // shortcut over the skip's channels, 1x1
+  bool ok = false;
+};
+
 struct UNet {
   UNetDesc d;
   int precision = 0;
   bool split = false;   // IDF_BF16X3
   int max_batch = 0;
   std::vector<ConvW> convs;
+  std::vector<DecW> dec;  // decoder blocks from the deepest level up (tensor-core precisions)
   std::vector<LevelBufs> lv;
   float2* stats = nullptr;
   double2* gnpart = nullptr;  // GroupNorm partials (scratch), max_batch * groups * GN_MAX_CHUNKS
@@ -1317,11 +1326,18 @@ static bool ck(cudaError_t e, Err* err, const char* what) {
 
 void unet_destroy(UNet* u) {
   if (!u) return;
-  for (auto& c : u->convs) {
+  auto free_w = [](ConvW& c) {
     cudaFree(c.w32);
     cudaFree(c.w16);
     cudaFree(c.w16lo);
     cudaFree(c.wtf);
+  };
+  for (auto& c : u->convs) free_w(c);
+  for (auto& dw : u->dec) {
+    free_w(dw.w1s);
+    for (auto& c : dw.w1p) free_w(c);
+    free_w(dw.wska);
+    free_w(dw.wsks);
   }
   if (u->own_bufs)
     for (auto& b : u->lv) {
@@ -1349,6 +1365,96 @@ size_t unet_arena_bytes(const UNetDesc& d, int precision, int max_batch) {
   return t;
 }
 
+// Tensor-core weight layout of one convolution, from (Cout, Cin, kh, kw)
+// float32 weights: [tap][Cout][Cin] bfloat16 (and the low parts with the
+// compensated split) or float32 rounded to tf32.
+static bool pack_tc(ConvW& c, const float* src, int precision, Err* err) {
+  const int taps = c.ks * c.ks;
+  const size_t n = (size_t)taps * c.cout * c.cin;
+  if (precision == 1 || precision == 3) {
+    std::vector<bf16> p16(n), p16lo(n);
+    for (int o = 0; o < c.cout; ++o)
+      for (int ci = 0; ci < c.cin; ++ci)
+        for (int t = 0; t < taps; ++t) {
+          const float v = src[((size_t)o * c.cin + ci) * taps + t];
+          const bf16 hi = __float2bfloat16_rn(v);
+          p16[((size_t)t * c.cout + o) * c.cin + ci] = hi;
+          p16lo[((size_t)t * c.cout + o) * c.cin + ci] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+    if (!ck(cudaMalloc(&c.w16, n * 2), err, "cudaMalloc bf16 weights") ||
+        !ck(cudaMemcpy(c.w16, p16.data(), n * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights"))
+      return false;
+    if (precision == 3 &&
+        (!ck(cudaMalloc(&c.w16lo, n * 2), err, "cudaMalloc bf16 weights") ||
+         !ck(cudaMemcpy(c.w16lo, p16lo.data(), n * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")))
+      return false;
+  } else if (precision == 4) {
+    std::vector<float> pt(n);
+    for (int o = 0; o < c.cout; ++o)
+      for (int ci = 0; ci < c.cin; ++ci)
+        for (int t = 0; t < taps; ++t) {
+          uint32_t u;
+          const float v = src[((size_t)o * c.cin + ci) * taps + t];
+          std::memcpy(&u, &v, 4);
+          u = tf32_rna_bits_host(u);
+          std::memcpy(&pt[((size_t)t * c.cout + o) * c.cin + ci], &u, 4);
+        }
+    if (!ck(cudaMalloc(&c.wtf, n * 4), err, "cudaMalloc tf32 weights") ||
+        !ck(cudaMemcpy(c.wtf, pt.data(), n * 4, cudaMemcpyHostToDevice), err, "copy tf32 weights"))
+      return false;
+  } else {
+    return false;
+  }
+  c.tc = true;
+  return true;
+}
+
+// Half-resolution form of a decoder ResBlock on [up2(a) (Ca), b (Cb)] ->
+// Cout: conv1 = conv3x3_b(n_b) + the four phase convolutions of n_a (a
+// 3x3 convolution of a nearest-upsampled input equals, for each output
+// phase (py, px), a 2x2 convolution of the input whose taps are the sums of
+// the 3x3 taps that read the same input pixel); shortcut = up2(W_a a) + W_b b.
+static bool make_dec_weights(DecW& dw, const float* w1, const float* wsk, int Ca, int Cb, int Cout, int precision,
+                             Err* err) {
+  const int Cin = Ca + Cb;
+  std::vector<float> t;
+  dw.w1s.cin = Cb; dw.w1s.cout = Cout; dw.w1s.ks = 3;
+  t.assign((size_t)Cout * Cb * 9, 0.f);
+  for (int o = 0; o < Cout; ++o)
+    for (int cj = 0; cj < Cb; ++cj)
+      for (int k = 0; k < 9; ++k) t[((size_t)o * Cb + cj) * 9 + k] = w1[((size_t)o * Cin + Ca + cj) * 9 + k];
+  if (!pack_tc(dw.w1s, t.data(), precision, err)) return false;
+  for (int py = 0; py < 2; ++py)
+    for (int px = 0; px < 2; ++px) {
+      ConvW& cp = dw.w1p[2 * py + px];
+      cp.cin = Ca; cp.cout = Cout; cp.ks = 2;
+      std::vector<double> acc((size_t)Cout * Ca * 4, 0.0);
+      for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+          // input row offset floor((py + dy) / 2) with dy = ky - 1, relative
+          // to the phase's first tap row py - 1
+          const int ry = py + ky - 1, rx = px + kx - 1;
+          const int ty = (ry < 0 ? -1 : ry / 2) - (py - 1), tx = (rx < 0 ? -1 : rx / 2) - (px - 1);
+          for (int o = 0; o < Cout; ++o)
+            for (int ci = 0; ci < Ca; ++ci)
+              acc[((size_t)o * Ca + ci) * 4 + ty * 2 + tx] += w1[((size_t)o * Cin + ci) * 9 + ky * 3 + kx];
+        }
+      t.assign(acc.size(), 0.f);
+      for (size_t i = 0; i < acc.size(); ++i) t[i] = (float)acc[i];
+      if (!pack_tc(cp, t.data(), precision, err)) return false;
+    }
+  dw.wska.cin = Ca; dw.wska.cout = Cout; dw.wska.ks = 1;
+  dw.wsks.cin = Cb; dw.wsks.cout = Cout; dw.wsks.ks = 1;
+  std::vector<float> ta((size_t)Cout * Ca), tb((size_t)Cout * Cb);
+  for (int o = 0; o < Cout; ++o) {
+    for (int ci = 0; ci < Ca; ++ci) ta[(size_t)o * Ca + ci] = wsk[(size_t)o * Cin + ci];
+    for (int cj = 0; cj < Cb; ++cj) tb[(size_t)o * Cb + cj] = wsk[(size_t)o * Cin + Ca + cj];
+  }
+  if (!pack_tc(dw.wska, ta.data(), precision, err) || !pack_tc(dw.wsks, tb.data(), precision, err)) return false;
+  dw.ok = true;
+  return true;
+}
+
 UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max_batch, Err* err,
                   void* arena, size_t arena_bytes) {
   UNet* u = new UNet();
@@ -1360,7 +1466,7 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
   const bool tfm = precision == 4;
   auto shapes = unet_param_shapes(d);
   size_t off = 0;
-  // resolution of each conv, to know whether the tensor-core kernel applies
+  std::vector<size_t> conv_off;
   for (auto& s : shapes) {
     ConvW c;
     c.cout = s[0];
@@ -1376,43 +1482,36 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
           pk[((size_t)t * c.cin + ci) * c.cout + o] = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
     if (!ck(cudaMalloc(&c.w32, pk.size() * 4), err, "cudaMalloc weights")) { unet_destroy(u); return nullptr; }
     if (!ck(cudaMemcpy(c.w32, pk.data(), pk.size() * 4, cudaMemcpyHostToDevice), err, "copy weights")) { unet_destroy(u); return nullptr; }
-    if (bfm && conv_tc_supported(c.cin, c.cout, c.ks)) {
-      // (Cout, Cin, kh, kw) -> [tap][Cout][Cin] bfloat16 (and the low parts)
-      std::vector<bf16> p16((size_t)taps * c.cout * c.cin), p16lo(p16.size());
-      for (int o = 0; o < c.cout; ++o)
-        for (int ci = 0; ci < c.cin; ++ci)
-          for (int t = 0; t < taps; ++t) {
-            const float v = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
-            const bf16 hi = __float2bfloat16_rn(v);
-            p16[((size_t)t * c.cout + o) * c.cin + ci] = hi;
-            p16lo[((size_t)t * c.cout + o) * c.cin + ci] = __float2bfloat16_rn(v - __bfloat162float(hi));
-          }
-      if (!ck(cudaMalloc(&c.w16, p16.size() * 2), err, "cudaMalloc bf16 weights")) { unet_destroy(u); return nullptr; }
-      if (!ck(cudaMemcpy(c.w16, p16.data(), p16.size() * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")) { unet_destroy(u); return nullptr; }
-      if (u->split) {
-        if (!ck(cudaMalloc(&c.w16lo, p16lo.size() * 2), err, "cudaMalloc bf16 weights")) { unet_destroy(u); return nullptr; }
-        if (!ck(cudaMemcpy(c.w16lo, p16lo.data(), p16lo.size() * 2, cudaMemcpyHostToDevice), err, "copy bf16 weights")) { unet_destroy(u); return nullptr; }
-      }
-      c.tc = true;
+    if ((bfm || tfm) && conv_tc_supported(c.cin, c.cout, c.ks) && !pack_tc(c, w_host + off, precision, err)) {
+      unet_destroy(u);
+      return nullptr;
     }
-    if (tfm && conv_tc_supported(c.cin, c.cout, c.ks)) {
-      // (Cout, Cin, kh, kw) -> [tap][Cout][Cin] float32 rounded to tf32
-      std::vector<float> pt((size_t)taps * c.cout * c.cin);
-      for (int o = 0; o < c.cout; ++o)
-        for (int ci = 0; ci < c.cin; ++ci)
-          for (int t = 0; t < taps; ++t) {
-            uint32_t u;
-            const float v = w_host[off + ((size_t)o * c.cin + ci) * taps + t];
-            std::memcpy(&u, &v, 4);
-            u = tf32_rna_bits_host(u);
-            std::memcpy(&pt[((size_t)t * c.cout + o) * c.cin + ci], &u, 4);
-          }
-      if (!ck(cudaMalloc(&c.wtf, pt.size() * 4), err, "cudaMalloc tf32 weights")) { unet_destroy(u); return nullptr; }
-      if (!ck(cudaMemcpy(c.wtf, pt.data(), pt.size() * 4, cudaMemcpyHostToDevice), err, "copy tf32 weights")) { unet_destroy(u); return nullptr; }
-      c.tc = true;
-    }
+    conv_off.push_back(off);
     off += (size_t)c.cout * c.cin * taps;
     u->convs.push_back(c);
+  }
+  if (bfm || tfm) {
+    // decoder blocks: conv1, conv2, shortcut, in the order unet_param_shapes lists them
+    size_t idx = 1;
+    int prev = d.ch[0];
+    for (int l = 0; l < d.levels; ++l) {
+      idx += 2 + (prev != d.ch[l] ? 1 : 0);
+      prev = d.ch[l];
+    }
+    idx += (d.attn ? 2 : 0) + 2;
+    for (int l = d.levels - 2; l >= 0; --l, idx += 3) {
+      DecW dw;
+      const int Ca = prev, Cb = d.ch[l], Co = d.ch[l];
+      if (conv_tc_supported(Ca, Co, 2) && conv_tc_supported(Cb, Co, 3) && conv_tc_supported(Cb, Co, 1) &&
+          conv_tc_supported(Ca, Co, 1) &&
+          !make_dec_weights(dw, w_host + conv_off[idx], w_host + conv_off[idx + 2], Ca, Cb, Co, precision, err)) {
+        u->dec.push_back(dw);
+        unet_destroy(u);
+        return nullptr;
+      }
+      u->dec.push_back(dw);
+      prev = Co;
+    }
   }
   const size_t B = (size_t)u->max_batch;
   size_t carve = 0;
@@ -1494,7 +1593,7 @@ bool tc_path(const ConvW& w, int H) {
 template <typename TA>
 bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H,
               const void* x_lo = nullptr, float2* bs = nullptr, const ConvW* w2 = nullptr,
-              const void* x2 = nullptr, const void* x2_lo = nullptr) {
+              const void* x2 = nullptr, const void* x2_lo = nullptr, const TcGeom* geom = nullptr) {
   if (!c.ok) return false;
   const int W = H;
   const double flops = 2.0 * c.n * H * W * (double)w.cout * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0));
@@ -1511,7 +1610,7 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     const bool ok = conv_tc_forward(x, wk, sp ? x_lo : nullptr, sp ? w.w16lo : nullptr, res, y, bs, c.n, H, W,
                                     w.cin, w.cout, w.ks, c.u->status, c.st, &e, w2 ? x2 : nullptr, wk2,
                                     w2 && sp ? x2_lo : nullptr, w2 && sp ? w2->w16lo : nullptr,
-                                    w2 ? w2->cin : 0, tf);
+                                    w2 ? w2->cin : 0, tf, geom);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     if (!ok) {
       c.ok = false;
@@ -1521,10 +1620,10 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     c.u->launches++;
     return ok && bs != nullptr;
   }
-  if (w2) {
+  if (w2 || geom) {
     c.ok = false;
     c.err->code = 3;
-    c.err->msg = "folded 1x1 operand outside the tensor-core path";
+    c.err->msg = "folded operand or convolution geometry outside the tensor-core path";
     return false;
   }
   const int64_t M = (int64_t)c.n * H * W;
@@ -1593,14 +1692,15 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
 // (one group's share) per thread.
 template <typename TA>
 void gn_apply_launch(Ctx& c, const float* x, int HW, int C, bool silu, void* y, void* copy, void* ylo,
-                     void* copylo) {
+                     void* copylo, int Cg = 0, int coff = 0) {
   const int G = c.u->d.groups;
+  if (Cg == 0) Cg = C / G;
   const int64_t units = (int64_t)c.n * HW * (C / 8);
   const int upw = HW * (C / 8);
   if (silu)
-    gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, Cg, coff, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
   else
-    gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    gn_apply8_kernel<TA, false><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, Cg, coff, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
 }
 
 // y (TA) = silu(gn(x)) or gn(x); copy (TA, optional) = x
@@ -1777,6 +1877,70 @@ bool resblock_cat(Ctx& c, size_t& wi, const LevelBufs& lb, const float* a, int C
   return true;
 }
 
+// Decoder ResBlock on [up2(a), b] with its upsampled branch at half
+// resolution (tensor-core precisions; weights from make_dec_weights):
+//   n_a, n_b  = silu(gn(.)) of the two parts with the concat's group
+//               statistics (n_a at a's own resolution) and operand copies;
+//   R1        = the four phase convolutions of n_a (2x2, half resolution),
+//               each scattered to its output phase at full resolution;
+//   T2        = conv3x3(n_b) + R1 (with GroupNorm block partials);
+//   R2        = the 1x1 shortcut of a's copy, half resolution;
+//   Y         = conv3x3(silu(gn(T2))) + the 1x1 shortcut of b's copy
+//               (folded) + up2(R2) (read in the epilogue).
+// This is the same function as conv3x3 over the materialised concat (both
+// maps are linear and commute with nearest upsampling) at 18% fewer FLOPs
+// for the fine UNet and without the upsampled channels at full resolution.
+// lh: the buffers of the half-resolution level (free at this point).
+// Returns false (having launched nothing) when a condition does not hold.
+template <typename TA>
+bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs& lh, const DecW& dw,
+                       const float* a, int Ca, const float* b, int Cb, int cout, float* Y, const float2* bsa,
+                       const float2* bsb, float2* bsY, bool* y_stats) {
+  const int G = c.u->d.groups, C = Ca + Cb, Cg = C / G, H = lb.H, Hh = H / 2;
+  if (std::is_same<TA, float>::value || !dw.ok || !bsa || !bsb || Ca + Cb == cout) return false;
+  const ConvW& c2 = c.u->convs[wi + 1];
+  if (!(C % G == 0 && Cg % 16 == 0 && Ca % 16 == 0 && Cb % 16 == 0 && (Hh * Hh) % 32 == 0 &&
+        tc_path<TA>(dw.w1p[0], Hh) && tc_path<TA>(dw.w1s, H) && tc_path<TA>(c2, H) &&
+        lh.cmax >= (size_t)std::max(Ca, cout) && lb.cmax >= (size_t)std::max(Cb, cout)))
+    return false;
+  wi += 3;
+  if (!c.ok) return true;
+  const bool sp = c.u->split;
+  // statistics of the concat's groups from the block partials of a and b
+  const double wr = (double)sizeof(TA) * 2 * (sp ? 2 : 1);
+  const double nb = (double)c.n * ((double)Hh * Hh * Ca + (double)H * H * Cb);
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (4.0 + wr)) : -1;
+  const BlkSrc bsrc{bsa, bsb, Ca, Cb, Hh * Hh / 32, H * H / 32};
+  gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(bsrc, c.n, G, c.u->stats);
+  gn_apply_launch<TA>(c, a, Hh * Hh, Ca, true, lh.T1, lh.T4, sp ? lh.T1lo : nullptr, sp ? lh.T4lo : nullptr, Cg, 0);
+  gn_apply_launch<TA>(c, b, H * H, Cb, true, lb.T1, lb.T4, sp ? lb.T1lo : nullptr, sp ? lb.T4lo : nullptr, Cg, Ca);
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+  c.u->launches += 3;
+  for (int py = 0; py < 2; ++py)
+    for (int px = 0; px < 2; ++px) {
+      TcGeom g;
+      g.oy = py - 1;
+      g.ox = px - 1;
+      g.out_up = 1;
+      g.py = py;
+      g.px = px;
+      conv_run<TA>(c, dw.w1p[2 * py + px], lh.T1, false, nullptr, (float*)lb.T3, Hh, sp ? lh.T1lo : nullptr,
+                   nullptr, nullptr, nullptr, nullptr, &g);
+    }
+  const bool s2 = conv_run<TA>(c, dw.w1s, lb.T1, false, (const float*)lb.T3, (float*)lb.T2, H,
+                               sp ? lb.T1lo : nullptr, lb.bT2);
+  gn<TA>(c, (const float*)lb.T2, H, cout, lb.T1, true, nullptr, sp ? lb.T1lo : nullptr, nullptr,
+         s2 ? lb.bT2 : nullptr);
+  conv_run<TA>(c, dw.wska, lh.T4, false, nullptr, (float*)lh.T2, Hh, sp ? lh.T4lo : nullptr);
+  TcGeom g2;
+  g2.oy = -1;
+  g2.ox = -1;
+  g2.res_up = 1;
+  *y_stats = conv_run<TA>(c, c2, lb.T1, false, (const float*)lh.T2, Y, H, sp ? lb.T1lo : nullptr, bsY, &dw.wsks,
+                          lb.T4, sp ? lb.T4lo : nullptr, &g2);
+  return true;
+}
+
 // ResBlock: X (cin, float32) -> Y (cout, float32).  bsX: block partials of X
 // (or null); bsY: where to write those of Y; returns whether they were.
 template <typename TA>
@@ -1863,9 +2027,17 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   m_st[L - 1] = resblock<TA>(c, wi, bl, cur, prev, prev, (float*)bl.M, cur_bs, bl.bM);
   for (int l = L - 2; l >= 0; --l) {
     LevelBufs& b = u->lv[l];
+    const float2* bsa = m_st[l + 1] ? u->lv[l + 1].bM : nullptr;
+    const float2* bsb = sk_st[l] ? b.bSK : nullptr;
+    const size_t di = (size_t)(L - 2 - l);
+    if (di < u->dec.size() &&
+        resblock_cat_half<TA>(c, wi, b, u->lv[l + 1], u->dec[di], (const float*)u->lv[l + 1].M, prev,
+                              (const float*)b.SK, d.ch[l], d.ch[l], (float*)b.M, bsa, bsb, b.bM, &m_st[l])) {
+      prev = d.ch[l];
+      continue;
+    }
     if (resblock_cat<TA>(c, wi, b, (const float*)u->lv[l + 1].M, prev, (const float*)b.SK, d.ch[l], d.ch[l],
-                         (float*)b.M, m_st[l + 1] ? u->lv[l + 1].bM : nullptr, sk_st[l] ? b.bSK : nullptr,
-                         b.bM, &m_st[l])) {
+                         (float*)b.M, bsa, bsb, b.bM, &m_st[l])) {
       prev = d.ch[l];
       continue;
     }
@@ -1938,9 +2110,9 @@ void launch_gn_f32(const float* x, int n, int H, int C, int G, bool silu, double
     gn_finalize_kernel<<<(n * G + 3) / 4, 128, 0, st>>>(x, part, n, chunks, HW, C, G, stats);
     const int upw = HW * (C / 8);
     if (silu)
-      gn_apply8_kernel<float, true><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, y, nullptr, nullptr, nullptr);
+      gn_apply8_kernel<float, true><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, C / G, 0, y, nullptr, nullptr, nullptr);
     else
-      gn_apply8_kernel<float, false><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, y, nullptr, nullptr, nullptr);
+      gn_apply8_kernel<float, false><<<grid1d(units, 256), 256, 0, st>>>(x, stats, (int)units, upw, C, G, C / G, 0, y, nullptr, nullptr, nullptr);
     return;
   }
   gn_stats_kernel<float><<<n * G, 256, 0, st>>>(x, HW, C, G, stats);
