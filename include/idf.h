@@ -124,7 +124,8 @@ typedef struct {
   idf_precision precision;          /* arithmetic of the UNet convolutions */
   size_t cache_bytes;               /* device tile cache; 0 = default (8 GiB) */
   int32_t device;                   /* CUDA device ordinal */
-  size_t workspace_bytes;           /* UNet activation arena shared by the levels; 0 = 64 GiB */
+  size_t workspace_bytes;           /* UNet activation arena shared by the levels; 0 = 128 GiB or
+                                       45% of the device's free memory, whichever is less */
   int32_t max_batch;                /* windows per UNet launch; 0 = from workspace */
   int32_t profile;                  /* 1: time every kernel launch with CUDA events on the
                                        world's stream; per-class totals in idf_world_stats */

@@ -1069,6 +1069,109 @@ __global__ void attention_d_kernel(const float* __restrict__ qkv, int Tn, int C,
   }
 }
 
+// Attention with two threads per query: lanes 2t and 2t + 1 each own half
+// of the head's D dimensions of query t (its q and output accumulator in
+// registers) and combine their partial scores with one shuffle, so a CTA
+// holds 2 x Tn threads at half the registers of one thread per query.  Keys
+// and values are staged as two half-rows per token, the second skewed by 16
+// bytes so that the pair's reads fall in different banks.  Softmax as in
+// attention_d_kernel: keys in blocks of four, one running-max update per
+// block.
+template <typename T, int D>
+__global__ void __launch_bounds__(512) attention_d2_kernel(const float* __restrict__ qkv, int Tn, int C,
+                                                           int heads, T* __restrict__ out,
+                                                           T* __restrict__ out_lo) {
+  extern __shared__ float sm[];
+  constexpr int DH = D / 2, RS = D + 8, HS = DH + 4;  // row stride, half-row offset (floats)
+  const int b = blockIdx.x / heads, h = blockIdx.x % heads;
+  float* Ks = sm;
+  float* Vs = sm + (size_t)Tn * RS;
+  const float* base = qkv + (int64_t)b * Tn * 3 * C;
+  for (int e = threadIdx.x; e < Tn * D / 4; e += blockDim.x) {
+    const int t = (4 * e) / D, c = (4 * e) % D;
+    const int o = t * RS + (c / DH) * HS + (c % DH);
+    *reinterpret_cast<float4*>(Ks + o) = *reinterpret_cast<const float4*>(base + (int64_t)t * 3 * C + C + h * D + c);
+    *reinterpret_cast<float4*>(Vs + o) = *reinterpret_cast<const float4*>(base + (int64_t)t * 3 * C + 2 * C + h * D + c);
+  }
+  __syncthreads();
+  const int t = threadIdx.x >> 1, hf = threadIdx.x & 1;  // blockDim.x == 2 Tn
+  const float scale = rsqrtf((float)D);
+  float q[DH], o[DH];
+  const float* qp = base + (int64_t)t * 3 * C + h * D + hf * DH;
+#pragma unroll
+  for (int c = 0; c < DH; ++c) {
+    q[c] = qp[c] * scale;
+    o[c] = 0.0f;
+  }
+  float mx = -INFINITY, den = 0.0f;
+  constexpr int KB = 4;
+  const float* kb = Ks + hf * HS;
+  const float* vb = Vs + hf * HS;
+  for (int j = 0; j < Tn; j += KB) {  // Tn % KB == 0
+    float sc[KB];
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const float4* kj = reinterpret_cast<const float4*>(kb + (size_t)(j + u) * RS);
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int c = 0; c < DH / 4; c += 2) {
+        const float4 k4 = kj[c], k5 = kj[c + 1];
+        a0 = fmaf(q[4 * c], k4.x, a0);
+        a1 = fmaf(q[4 * c + 4], k5.x, a1);
+        a0 = fmaf(q[4 * c + 1], k4.y, a0);
+        a1 = fmaf(q[4 * c + 5], k5.y, a1);
+        a0 = fmaf(q[4 * c + 2], k4.z, a0);
+        a1 = fmaf(q[4 * c + 6], k5.z, a1);
+        a0 = fmaf(q[4 * c + 3], k4.w, a0);
+        a1 = fmaf(q[4 * c + 7], k5.w, a1);
+      }
+      const float part = a0 + a1;
+      // both lanes add the two halves in the same order: equal scores
+      const float other = __shfl_xor_sync(0xffffffffu, part, 1);
+      sc[u] = hf ? other + part : part + other;
+    }
+    float bm = sc[0];
+#pragma unroll
+    for (int u = 1; u < KB; ++u) bm = fmaxf(bm, sc[u]);
+    if (bm > mx) {
+      const float corr = expf(mx - bm);
+      den *= corr;
+#pragma unroll
+      for (int c = 0; c < DH; ++c) o[c] *= corr;
+      mx = bm;
+    }
+    float pj[KB];
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      pj[u] = expf(sc[u] - mx);
+      den += pj[u];
+    }
+#pragma unroll
+    for (int c = 0; c < DH / 4; ++c) {
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        const float4 v4 = reinterpret_cast<const float4*>(vb + (size_t)(j + u) * RS)[c];
+        o[4 * c] = fmaf(pj[u], v4.x, o[4 * c]);
+        o[4 * c + 1] = fmaf(pj[u], v4.y, o[4 * c + 1]);
+        o[4 * c + 2] = fmaf(pj[u], v4.z, o[4 * c + 2]);
+        o[4 * c + 3] = fmaf(pj[u], v4.w, o[4 * c + 3]);
+      }
+    }
+  }
+  const float inv = 1.0f / den;
+  T* op = out + ((int64_t)b * Tn + t) * C + h * D + hf * DH;
+#pragma unroll
+  for (int c = 0; c < DH; ++c) st<T>(op + c, o[c] * inv);
+  if (out_lo) {
+    T* ol = out_lo + ((int64_t)b * Tn + t) * C + h * D + hf * DH;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+      const float v = o[c] * inv;
+      st<T>(ol + c, v - ld<T>(op + c));
+    }
+  }
+}
+
 // ------------------------------------------------------------ resampling
 template <typename T>
 __global__ void avgpool2_kernel(const T* __restrict__ x, int n, int H, int W, int C,
@@ -2007,7 +2110,13 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     const int Tn = bl.H * bl.H, dh = prev / d.heads;
     const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
     const int pr = u->prof ? u->prof->begin(PK_ATTENTION, st, 4.0 * n * (double)Tn * Tn * prev, 0.0) : -1;
-    if (dh == 64 || dh == 32 || dh == 16) {
+    const size_t smem2 = (size_t)2 * Tn * (dh + 8) * sizeof(float);
+    if (dh == 64 && Tn % 4 == 0 && 2 * Tn <= 512 && smem2 <= 200 * 1024) {
+      auto kern = attention_d2_kernel<TA, 64>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+      kern<<<n * d.heads, 2 * Tn, smem2, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3,
+                                               u->split ? (TA*)bl.T3lo : nullptr);
+    } else if (dh == 64 || dh == 32 || dh == 16) {
       auto kern = dh == 64 ? attention_d_kernel<TA, 64> : dh == 32 ? attention_d_kernel<TA, 32> : attention_d_kernel<TA, 16>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<n * d.heads, std::min(Tn, 256), smem, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3,

@@ -817,7 +817,15 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
   if (cudaMalloc(&W->d_err, sizeof(int)) != cudaSuccess || cudaMemset(W->d_err, 0, sizeof(int)) != cudaSuccess)
     return bail(IDF_ECUDA);
   const size_t cache_bytes = opts->cache_bytes ? opts->cache_bytes : ((size_t)8 << 30);
-  const size_t ws_bytes = opts->workspace_bytes ? opts->workspace_bytes : ((size_t)64 << 30);
+  // default arena: 128 GiB, or 45% of the device's free memory if that is
+  // less (larger window batches amortise the per-launch ramp of the
+  // persistent convolutions; results do not depend on the batch)
+  size_t ws_bytes = opts->workspace_bytes;
+  if (!ws_bytes) {
+    size_t fr = 0, tot = 0;
+    ws_bytes = (size_t)64 << 30;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) ws_bytes = std::min((size_t)128 << 30, fr / 100 * 45);
+  }
   // one activation arena shared by the levels' UNets (they never run at the
   // same time): each level batches as many windows as the arena holds
   size_t arena_need = 0;
