@@ -35,7 +35,7 @@ WORKLOAD = ("2-level hierarchy (coarse 64/128/128 @1/8, fine 64/128/256/256 + at
             "128x128 windows stride 64, 20 steps, 4096x4096 metres query, tensor-core convs")
 # max abs error vs the FP64 oracle on the full-width stack (2 blended steps,
 # the worst case), in sigma_out, as the GPU parity tests measure it
-STATED_ERROR = {"fp32": 1.0e-5, "tf32": 4.1e-3, "bf16x3": 9.3e-5, "bf16": 3.3e-2}
+STATED_ERROR = {"fp32": 1.5e-5, "tf32": 4.5e-3, "bf16x3": 9.1e-5, "bf16": 3.7e-2}
 
 
 def bench_config(q: int, precision: str, windows_per_step=None, world: int = 1) -> dict:
