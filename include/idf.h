@@ -101,7 +101,8 @@ typedef struct {
 /*
  * A chain of levels, coarse first (at most 2).  laplacian = 1 (two levels)
  * reads level 0 as the normalised low band L and level 1 as the normalised
- * residual H of the Laplacian encoding (Sec. 5.2) and enables
+ * residual H of the Laplacian encoding (Sec. 5.2; with one level and a
+ * low_band_fixture, L comes from the fixture) and enables
  * IDF_OUT_METRES: l = low_mu + low_scale L, h = res_scale H,
  * P = up(l) + h, l^ = blur(down(P)), v = up(l^) + h, metres = sign(v) v^2
  * (App. H), with down = mean over lap_factor^2 blocks, blur = Gaussian of
@@ -118,6 +119,13 @@ typedef struct {
   int32_t lap_radius;
   double low_mu, low_scale, res_scale;
   double blend_eps;
+  /* Optional given low band (a single-level stack with laplacian = 1): a
+   * host array of fixture_period^2 float32 normalised low-band values L on
+   * the low-resolution grid, row-major, read periodically
+   * (L(x, y) = fixture[(y mod P) * P + (x mod P)]), copied at create time.
+   * The single level is then the residual band H.  NULL / 0 otherwise. */
+  const float* low_band_fixture;
+  int64_t fixture_period;
 } idf_model_stack;
 
 typedef struct {

@@ -207,10 +207,16 @@ class World:
         return self.levels[-1].final(y0, x0, h, w)
 
     def metres(self, y0, x0, h, w):
+        """Laplacian decode (Sec. 5.2, App. H) of the last level's residual
+        band with the first level's low band, or, for a single level with a
+        given low band (stack["low_band_fixture"], a periodic low-resolution
+        array), with that array read periodically."""
         from . import laplacian as L_
         st = self.stack
-        coarse, fine = self.levels[0], self.levels[-1]
-        return L_.decode_metres(coarse.final, fine.final, y0, x0, h, w,
+        fine = self.levels[-1]
+        fx = st.get("low_band_fixture")
+        lfun = L_.periodic_lowband(fx) if fx is not None else self.levels[0].final
+        return L_.decode_metres(lfun, fine.final, y0, x0, h, w,
                                 factor=st["lap_factor"], blur_sigma=st["lap_blur_sigma"],
                                 radius=st["lap_radius"], low_mu=st["low_mu"],
                                 low_scale=st["low_scale"], res_scale=st["res_scale"])

@@ -60,6 +60,7 @@ class idf_model_stack(C.Structure):
         ("laplacian", C.c_int32), ("lap_factor", C.c_int32), ("lap_blur_sigma", C.c_double),
         ("lap_radius", C.c_int32), ("low_mu", C.c_double), ("low_scale", C.c_double),
         ("res_scale", C.c_double), ("blend_eps", C.c_double),
+        ("low_band_fixture", C.POINTER(C.c_float)), ("fixture_period", C.c_int64),
     ]
 
 
@@ -168,6 +169,15 @@ def model_stack(st: dict, weights: Optional[Sequence] = None, keep: Optional[_Ke
     s.laplacian, s.lap_factor, s.lap_blur_sigma, s.lap_radius = (
         st["laplacian"], st["lap_factor"], st["lap_blur_sigma"], st["lap_radius"])
     s.low_mu, s.low_scale, s.res_scale, s.blend_eps = st["low_mu"], st["low_scale"], st["res_scale"], st["blend_eps"]
+    fx = st.get("low_band_fixture")
+    if fx is not None:
+        import numpy as np
+        fx = np.ascontiguousarray(fx, dtype=np.float32)
+        if fx.ndim != 2 or fx.shape[0] != fx.shape[1]:
+            raise ValueError("low_band_fixture must be a square 2-D array")
+        keep.refs.append(fx)
+        s.low_band_fixture = fx.ctypes.data_as(C.POINTER(C.c_float))
+        s.fixture_period = fx.shape[0]
     keep.refs.append(s)
     return s
 

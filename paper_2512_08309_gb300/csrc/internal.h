@@ -97,6 +97,10 @@ struct DecodeArgs {
   int64_t qx0, qy0; int qw, qh;   // coarse rect of L^ that the output reads
 };
 void launch_decode(const DecodeArgs& a, cudaStream_t st);
+// dst[y * w + x] = fixture[((y0 + y) mod P) * P + ((x0 + x) mod P)] (a
+// periodic low-band fixture read over a rect of the low-resolution grid)
+void launch_fixture_gather(const float* fixture, int64_t P, int64_t x0, int64_t y0, int w, int h, float* dst,
+                           cudaStream_t st);
 
 // --------------------------------------------------------------- profiling
 // Optional per-launch CUDA-event timing on the launching stream, grouped by

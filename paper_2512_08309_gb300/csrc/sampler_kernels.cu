@@ -296,4 +296,24 @@ void launch_decode(const DecodeArgs& a, cudaStream_t st) {
   decode_final_kernel<<<grid_for((int64_t)a.w * a.h, 256), 256, 0, st>>>(a);
 }
 
+// ---------------------------------------------------------------- fixture
+__global__ void fixture_gather_kernel(const float* __restrict__ fx, int64_t P, int64_t x0, int64_t y0, int w,
+                                      int h, float* __restrict__ dst) {
+  const int64_t n = (int64_t)w * h;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / w, x = i % w;
+    int64_t gy = (y0 + y) % P, gx = (x0 + x) % P;
+    if (gy < 0) gy += P;
+    if (gx < 0) gx += P;
+    dst[i] = fx[gy * P + gx];
+  }
+}
+
+void launch_fixture_gather(const float* fixture, int64_t P, int64_t x0, int64_t y0, int w, int h, float* dst,
+                           cudaStream_t st) {
+  const int64_t n = (int64_t)w * h;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (n > 0) fixture_gather_kernel<<<blocks, 256, 0, st>>>(fixture, P, x0, y0, w, h, dst);
+}
+
 }  // namespace idf

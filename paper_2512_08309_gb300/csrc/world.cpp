@@ -142,6 +142,7 @@ struct idf_world {
   float* dec = nullptr; size_t dec_cap = 0;        // decode scratch
   float* outbuf = nullptr; size_t out_cap = 0;     // for host-output queries
   float* d_taps = nullptr;
+  float* d_fixture = nullptr;                      // given low band (single-level Laplacian stack)
   int* d_err = nullptr;
   int32_t* h_tab = nullptr; size_t h_tab_cap = 0; // pinned staging
   void* arena = nullptr; size_t arena_bytes = 0;  // UNet activations, shared by the levels
@@ -685,6 +686,21 @@ idf_status serve(idf_world* W, const std::vector<Req>& reqs, idf_output_kind kin
         off += (size_t)hl.Lw * hl.Lh;
       }
   }
+  if (nl == 1 && kind == IDF_OUT_METRES) {
+    // given low band: read the periodic fixture over each decode's L rect
+    size_t need = 0;
+    for (auto& hl : halos) need += (size_t)hl.Lw * hl.Lh;
+    if (!grow(W, &W->dense, &W->dense_cap, need + 1, "low band")) return fail(W, IDF_ENOMEM, W->last_error);
+    size_t off = 0;
+    for (size_t i = 0; i < reqs.size(); ++i) {
+      const Halo& hl = halos[i];
+      lows[i] = Dense{W->dense + off, hl.Lx0, hl.Ly0, hl.Lw, (int)hl.Lw, (int)hl.Lh};
+      launch_fixture_gather(W->d_fixture, W->stack.fixture_period, hl.Lx0, hl.Ly0, (int)hl.Lw, (int)hl.Lh,
+                            lows[i].p, W->st);
+      W->launches++;
+      off += (size_t)hl.Lw * hl.Lh;
+    }
+  }
   if (!run_level(W, F, fp, nl == 2 && fp.any_windows ? &cond : nullptr))
     return fail(W, W->poisoned ? IDF_ECUDA : IDF_ENOMEM, W->last_error);
   for (size_t i = 0; i < reqs.size(); ++i) {
@@ -787,15 +803,22 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
     return IDF_EINVAL;
   if (!(stack->blend_eps > 0) || !(stack->blend_eps <= 1)) return IDF_EINVAL;
   if (stack->laplacian) {
-    if (stack->n_levels != 2 || stack->lap_factor < 2 || stack->lap_factor % 2 || stack->lap_radius < 0 ||
-        stack->lap_radius > 64 || !(stack->lap_blur_sigma > 0))
+    // two levels (L then H), or one level (H) with a given low band
+    const bool fixture = stack->n_levels == 1 && stack->low_band_fixture && stack->fixture_period >= 1 &&
+                         stack->fixture_period <= (1 << 15) && stack->level[0].in_ch == 1;
+    if ((stack->n_levels != 2 && !fixture) || (stack->n_levels == 2 && stack->low_band_fixture) ||
+        stack->lap_factor < 2 || stack->lap_factor % 2 || stack->lap_radius < 0 || stack->lap_radius > 64 ||
+        !(stack->lap_blur_sigma > 0))
       return IDF_EINVAL;
+  } else if (stack->low_band_fixture) {
+    return IDF_EINVAL;
   }
   std::unique_ptr<idf_world> W(new (std::nothrow) idf_world());
   if (!W) return IDF_ENOMEM;
   W->seed = seed;
   W->stack = *stack;
   W->stack.level = nullptr;
+  W->stack.low_band_fixture = nullptr;  // copied to W->d_fixture below
   W->opts = *opts;
   for (int i = 0; i < stack->n_levels; ++i) {
     const idf_level_desc& d = stack->level[i];
@@ -912,6 +935,12 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
     auto taps = blur_taps(stack->lap_blur_sigma, stack->lap_radius);
     if (cudaMalloc(&W->d_taps, taps.size() * 4) != cudaSuccess) return bail(IDF_ENOMEM);
     cudaMemcpy(W->d_taps, taps.data(), taps.size() * 4, cudaMemcpyHostToDevice);
+    if (stack->low_band_fixture) {
+      const size_t nf = (size_t)stack->fixture_period * stack->fixture_period;
+      if (cudaMalloc(&W->d_fixture, nf * 4) != cudaSuccess) return bail(IDF_ENOMEM);
+      if (cudaMemcpy(W->d_fixture, stack->low_band_fixture, nf * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(IDF_ECUDA);
+    }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(IDF_ECUDA);
   *out = W.release();
@@ -928,7 +957,7 @@ void idf_world_destroy(idf_world* W) {
     cudaFree(L.cache.pool);
   }
   cudaFree(W->F); cudaFree(W->x_in); cudaFree(W->tab); cudaFree(W->dense); cudaFree(W->dec);
-  cudaFree(W->outbuf); cudaFree(W->d_taps); cudaFree(W->d_err); cudaFree(W->arena);
+  cudaFree(W->outbuf); cudaFree(W->d_taps); cudaFree(W->d_fixture); cudaFree(W->d_err); cudaFree(W->arena);
   if (W->h_tab) cudaFreeHost(W->h_tab);
   if (W->ev_join) cudaEventDestroy(W->ev_join);
   if (W->st) cudaStreamDestroy(W->st);

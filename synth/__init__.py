@@ -90,6 +90,19 @@ def small_hier_stack(steps: int = 3, window: int = 32, stride: int = 16,
     return stack([coarse, fine], laplacian=1)
 
 
+def config4_stack(fixture: np.ndarray, steps: int = 4, test_denoiser: int = 0) -> dict:
+    """Earth-scale single-level stack: the 16-channel config-1 UNet generates
+    the residual band H (32x32 windows at stride 16) and the low band is the
+    given periodic fixture of signed-sqrt values (low_mu 0, low_scale 1), so
+    that the decoded metres span the fixture's range; Laplacian factor 8,
+    blur sigma 5, radius 15, residual scale 1.5."""
+    fine = level(levels=2, channels=(16, 16), in_ch=1, out_ch=1, window=32, stride=16, steps=steps,
+                 test_denoiser=test_denoiser)
+    st = stack([fine], laplacian=1, low_mu=0.0, low_scale=1.0, res_scale=1.5)
+    st["low_band_fixture"] = np.ascontiguousarray(fixture, dtype=np.float32)
+    return st
+
+
 def student_level(window: int = 128, stride: int = 64) -> dict:
     """The half-width 2-step student: 4 levels of 32/64/128/128 channels,
     128x128 windows at stride 64, sigma 80 then 0.35."""
