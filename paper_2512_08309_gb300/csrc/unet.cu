@@ -577,6 +577,106 @@ __global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const fl
   }
 }
 
+// ------------------------------------------------------------ small-channel convolution
+// 3x3 convolution with few output channels (C_out = 16 or 32), float32
+// accumulation.  A CTA owns R = 256 PX / W rows of one window, all columns
+// and all output channels; the (R + 2) x (W + 2) input neighbourhood is
+// staged channel-major in shared memory 16 channels at a time (zero outside
+// the window), with those channels' weights; thread t accumulates the PX
+// pixels t, t + 256, ... of the CTA's rows times all C_out channels, so that
+// each input value read from shared memory feeds C_out FMAs and each
+// (broadcast) weight quad feeds 4 PX.  res may alias y (each output element
+// is read, then written, by the one thread that owns it).
+template <int COUT, int PX, typename Tin>
+__global__ void __launch_bounds__(256) conv_small_kernel(const Tin* __restrict__ x, const Tin* __restrict__ xlo,
+                                                         const float* __restrict__ wk, const float* res, float* y,
+                                                         int H, int W, int Cin) {
+  constexpr int CC = 16;
+  extern __shared__ float sm[];
+  const int R = 256 * PX / W;
+  const int W2 = W + 2, RW = (R + 2) * W2;
+  float* xs = sm;            // [CC][R+2][W+2]
+  float* ws = sm + CC * RW;  // [9][CC][COUT]
+  const int r0 = blockIdx.x * R;
+  const int64_t b = blockIdx.y;
+  const Tin* xb = x + b * H * W * Cin;
+  const Tin* xlb = xlo ? xlo + b * H * W * Cin : nullptr;
+  int prow[PX], pcol[PX];
+#pragma unroll
+  for (int j = 0; j < PX; ++j) {
+    const int p = threadIdx.x + 256 * j;
+    prow[j] = p / W;
+    pcol[j] = p % W;
+  }
+  float acc[PX][COUT];
+#pragma unroll
+  for (int j = 0; j < PX; ++j)
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) acc[j][o] = 0.0f;
+  for (int c0 = 0; c0 < Cin; c0 += CC) {
+    __syncthreads();
+    // input: pixel p of the neighbourhood, channel quad q
+    for (int e = threadIdx.x; e < RW * (CC / 4); e += 256) {
+      const int p = e / (CC / 4), q = e % (CC / 4);
+      const int gy = r0 + p / W2 - 1, gx = p % W2 - 1;
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        const int64_t off = ((int64_t)gy * W + gx) * Cin + c0 + 4 * q;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          v[k] = ld<Tin>(xb + off + k);
+          if (xlb) v[k] += ld<Tin>(xlb + off + k);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xs[(4 * q + k) * RW + p] = v[k];
+    }
+    // weights of the chunk: wk is [tap * Cin + ci][COUT]
+    for (int e = threadIdx.x; e < 9 * CC * COUT; e += 256) {
+      const int o = e % COUT, ci = (e / COUT) % CC, tap = e / (COUT * CC);
+      ws[e] = wk[((int64_t)tap * Cin + c0 + ci) * COUT + o];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3;
+#pragma unroll 4
+      for (int ci = 0; ci < CC; ++ci) {
+        float xv[PX];
+#pragma unroll
+        for (int j = 0; j < PX; ++j) xv[j] = xs[ci * RW + (prow[j] + dy) * W2 + pcol[j] + dx];
+        const float4* wv = reinterpret_cast<const float4*>(ws + (tap * CC + ci) * COUT);
+#pragma unroll
+        for (int qd = 0; qd < COUT / 4; ++qd) {
+          const float4 w4 = wv[qd];
+#pragma unroll
+          for (int j = 0; j < PX; ++j) {
+            acc[j][4 * qd] = fmaf(xv[j], w4.x, acc[j][4 * qd]);
+            acc[j][4 * qd + 1] = fmaf(xv[j], w4.y, acc[j][4 * qd + 1]);
+            acc[j][4 * qd + 2] = fmaf(xv[j], w4.z, acc[j][4 * qd + 2]);
+            acc[j][4 * qd + 3] = fmaf(xv[j], w4.w, acc[j][4 * qd + 3]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < PX; ++j) {
+    const int64_t m = (b * H + r0 + prow[j]) * W + pcol[j];
+    float4* yp = reinterpret_cast<float4*>(y + m * COUT);
+    const float4* rp = res ? reinterpret_cast<const float4*>(res + m * COUT) : nullptr;
+#pragma unroll
+    for (int qd = 0; qd < COUT / 4; ++qd) {
+      float4 v = make_float4(acc[j][4 * qd], acc[j][4 * qd + 1], acc[j][4 * qd + 2], acc[j][4 * qd + 3]);
+      if (rp) {
+        const float4 r = rp[qd];
+        v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
+      }
+      yp[qd] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------ thin convolutions
 // In-conv (C_in <= 4 -> C_out): thread per (pixel, 4 output channels).
 template <int CIN>
@@ -1777,6 +1877,37 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches++;
     return false;
+  }
+  if (w.ks == 3 && (w.cout == 16 || w.cout == 32) && w.cin % 16 == 0 && (W == 16 || W == 32 || W == 64 || W == 128)) {
+    // small-channel path: PX pixels per thread, R = 256 PX / W rows per CTA
+    const int px = w.cout == 16 ? (1024 / W <= H ? 4 : 1) : (512 / W <= H ? 2 : 1);
+    const int R = 256 * px / W;
+    if (R >= 1 && H % R == 0) {
+      const size_t smem = ((size_t)16 * (R + 2) * (W + 2) + 9 * 16 * w.cout) * sizeof(float);
+      const dim3 grid(H / R, c.n);
+      if (x_f32) {
+        const float* xf = (const float*)x;
+        const float* xl = nullptr;
+        auto kf = [&](auto kern) {
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          kern<<<grid, 256, smem, c.st>>>(xf, xl, w.w32, res, y, H, W, w.cin);
+        };
+        if (w.cout == 16) (px == 4 ? kf(conv_small_kernel<16, 4, float>) : kf(conv_small_kernel<16, 1, float>));
+        else (px == 2 ? kf(conv_small_kernel<32, 2, float>) : kf(conv_small_kernel<32, 1, float>));
+      } else {
+        const TA* xt = (const TA*)x;
+        const TA* xl = (const TA*)x_lo;
+        auto kt = [&](auto kern) {
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          kern<<<grid, 256, smem, c.st>>>(xt, xl, w.w32, res, y, H, W, w.cin);
+        };
+        if (w.cout == 16) (px == 4 ? kt(conv_small_kernel<16, 4, TA>) : kt(conv_small_kernel<16, 1, TA>));
+        else (px == 2 ? kt(conv_small_kernel<32, 2, TA>) : kt(conv_small_kernel<32, 1, TA>));
+      }
+      if (c.u->prof) c.u->prof->end(pr, c.st);
+      c.u->launches++;
+      return false;
+    }
   }
   dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((w.cout + CBN - 1) / CBN));
   if (w.ks == 3) {
