@@ -464,6 +464,65 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
   }
 }
 
+// The apply pass for groups of 4 channels (the 16-channel network): one
+// float4 of x (one group's share of a pixel) per thread.
+template <typename TA> struct Pack4;
+template <> struct Pack4<float> {
+  static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Pack4<tf32> {
+  static __device__ __forceinline__ void store(tf32* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(tf32_rn(v[0]), tf32_rn(v[1]), tf32_rn(v[2]), tf32_rn(v[3]));
+  }
+};
+template <> struct Pack4<bf16> {
+  static __device__ __forceinline__ void store(bf16* p, const float (&v)[4]) {
+    uint2 u;
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
+    u.x = *reinterpret_cast<uint32_t*>(&h0);
+    u.y = *reinterpret_cast<uint32_t*>(&h1);
+    *reinterpret_cast<uint2*>(p) = u;
+  }
+};
+
+template <typename TA, bool SILU>
+__global__ void __launch_bounds__(256) gn_apply4_kernel(const float* __restrict__ x,
+                                                        const float2* __restrict__ stats, int n_units,
+                                                        int units_per_win, int C, int G, TA* __restrict__ y,
+                                                        TA* __restrict__ copy, TA* __restrict__ ylo,
+                                                        TA* __restrict__ copylo) {
+  const int C4 = C / 4, Cg = C / G;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+    const int b = u / units_per_win;
+    const int c0 = (u % C4) * 4;
+    const float2 ms = stats[b * G + c0 / Cg];
+    const float4 a = reinterpret_cast<const float4*>(x)[u];
+    const float xv[4] = {a.x, a.y, a.z, a.w};
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float z = (xv[j] - ms.x) * ms.y;
+      if (SILU) z = silu_fast(z);
+      v[j] = z;
+    }
+    Pack4<TA>::store(y + (int64_t)u * 4, v);
+    if (copy) Pack4<TA>::store(copy + (int64_t)u * 4, xv);
+    if (ylo) {
+      float r[4], rc[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        r[j] = v[j] - __bfloat162float(__float2bfloat16_rn(v[j]));
+        rc[j] = xv[j] - __bfloat162float(__float2bfloat16_rn(xv[j]));
+      }
+      Pack4<TA>::store(ylo + (int64_t)u * 4, r);
+      if (copylo) Pack4<TA>::store(copylo + (int64_t)u * 4, rc);
+    }
+  }
+}
+
 // GroupNorm of a virtual channel concat [nearest-up2(a) (Ca channels), b (Cb
 // channels)] at resolution H, without materialising it: the same passes as
 // above, each float4 / 8-channel unit reading from the source that holds its
@@ -1950,6 +2009,9 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
   const int Cg = C / G;
   const int64_t units = (int64_t)c.n * HW * (C / 8);
   const bool fast = C % 8 == 0 && Cg % 8 == 0 && Cg / 4 <= 256 && units < (1ll << 31);
+  // groups of 4 channels: the chunked statistics and a float4 apply pass
+  const int64_t units4 = (int64_t)c.n * HW * (C / 4);
+  const bool fast4 = !fast && C % 4 == 0 && Cg % 4 == 0 && Cg / 4 <= 256 && units4 < (1ll << 31);
   const bool blk = fast && bs && C % 16 == 0 && Cg % 16 == 0 && HW % 32 == 0;
   // algorithmic bytes: the apply pass reads the float32 input once and writes
   // the operand (and the copy, and their low parts); without block partials
@@ -1962,6 +2024,25 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
     gn_apply_launch<TA>(c, x, HW, C, silu, y, copy, ylo, copylo);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches += 2;
+    return;
+  }
+  if (fast4) {
+    const int Q = Cg / 4, P = 256 / Q;
+    int chunk_px = std::max(P, 8192 / Cg);
+    int chunks = (HW + chunk_px - 1) / chunk_px;
+    if (chunks > GN_MAX_CHUNKS) {
+      chunk_px = (HW + GN_MAX_CHUNKS - 1) / GN_MAX_CHUNKS;
+      chunks = (HW + chunk_px - 1) / chunk_px;
+    }
+    gn_partial_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(x, HW, C, G, chunk_px, c.u->gnpart);
+    gn_finalize_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
+    const int upw = HW * (C / 4);
+    if (silu)
+      gn_apply4_kernel<TA, true><<<grid1d(units4, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units4, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    else
+      gn_apply4_kernel<TA, false><<<grid1d(units4, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units4, upw, C, G, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches += 3;
     return;
   }
   if (fast) {
