@@ -398,6 +398,23 @@ def run_idf(args, rank, world, local):
             gbs = p["bytes"] / (p["ms"] / 1000.0) / 1e9
             hbm[k] = {"achieved_gbs": gbs, "frac": gbs / pk["hbm_gbs"], "launches": p["launches"],
                       "share_of_step": p["ms"] / ms}
+    # the blend draws one or two normals per pixel (Philox4x32-10 + Box-Muller,
+    # bit-exact by definition): its arithmetic, not memory, bounds it, so it is
+    # compared with the pure generator (idf_noise_fill over a 8192^2 region)
+    if prof["blend"]["ms"] > 0 and prof["blend"]["flops"] > 0:
+        nbuf = torch.empty((8192, 8192), dtype=torch.float32, device=dev)
+        idf.noise_fill(1, 0, 1, 0, 0, 8192, 8192, nbuf.data_ptr(), 8192, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(3):
+            idf.noise_fill(1, 0, 2 + i, 0, 0, 8192, 8192, nbuf.data_ptr(), 8192, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gen = 3 * 8192 * 8192 / (a.elapsed_time(b) / 1000.0)
+        del nbuf
+        rate = prof["blend"]["flops"] / (prof["blend"]["ms"] / 1000.0)
+        hbm["blend"].update({"bound": "alu (noise generation)", "normals_per_s": rate,
+                             "generator_normals_per_s": gen, "frac_of_generator": rate / gen})
 
     line = {
         "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,

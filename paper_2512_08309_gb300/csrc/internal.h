@@ -107,6 +107,9 @@ void launch_fixture_gather(const float* fixture, int64_t P, int64_t x0, int64_t 
 // kernel class, with the algorithmic FLOPs / bytes of each launch.
 enum ProfKind { PK_CONV_TC = 0, PK_CONV_SIMT, PK_GROUPNORM, PK_ATTENTION, PK_RESAMPLE,
                 PK_GATHER, PK_DENOISE_TEST, PK_BLEND, PK_ASSEMBLE, PK_DECODE, PK_COUNT };
+// One timed launch: flops = the class's work (FLOPs of the convolutions
+// and attention; for the blend, the normal samples it draws), bytes = its
+// algorithmic memory traffic.
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;

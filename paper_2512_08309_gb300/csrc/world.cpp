@@ -507,8 +507,11 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
     bl.seed = W->seed;
     bl.level = (uint32_t)L.index;
     // algorithmic bytes per tile pixel: r^2 window outputs, J_k (unless it is
-    // the noise) and J_{k+1}
-    const int pr = W->prof.begin(PK_BLEND, st, 0.0, (double)bl.n_tiles * s * s * 4.0 * (r * r + (k ? 2 : 1)));
+    // the noise) and J_{k+1}; the work field counts the normal samples drawn
+    // (J_0 at the first step, the re-noise before every later one), whose
+    // Philox + Box-Muller arithmetic, not memory, bounds this kernel
+    const double normals = (double)bl.n_tiles * s * s * ((k == 0 ? 1 : 0) + (k + 1 < K ? 1 : 0));
+    const int pr = W->prof.begin(PK_BLEND, st, normals, (double)bl.n_tiles * s * s * 4.0 * (r * r + (k ? 2 : 1)));
     launch_blend(bl, st);
     W->prof.end(pr, st);
     W->launches++;
