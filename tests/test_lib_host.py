@@ -63,3 +63,40 @@ def test_decode_halo_covers_oracle_reads(rect):
     lx0, lx1 = OL.up_range(px0, pw, f)
     assert Hr == (px0, py0, pw, ph)
     assert Lr == (lx0, ly0, lx1 - lx0 + 1, ly1 - ly0 + 1)
+
+
+@pytest.mark.parametrize("case", ["two_level_with_fixture", "fixture_without_laplacian",
+                                  "single_level_laplacian_without_fixture", "fixture_with_conditioned_level"])
+def test_world_create_rejects_invalid_low_band_setups(case):
+    # argument validation runs before any device call, so a bad stack is
+    # refused with IDF_EINVAL even without a GPU
+    import numpy as np
+    idf = _lib()
+    fx = np.zeros((8, 8), dtype=np.float32)
+    if case == "two_level_with_fixture":
+        st = synth.small_hier_stack(test_denoiser=1)
+        st["low_band_fixture"] = fx
+    elif case == "fixture_without_laplacian":
+        st = synth.config4_stack(fx, test_denoiser=1)
+        st["laplacian"] = 0
+    elif case == "single_level_laplacian_without_fixture":
+        st = synth.config4_stack(fx, test_denoiser=1)
+        st.pop("low_band_fixture")
+    else:
+        st = synth.config4_stack(fx, test_denoiser=1)
+        st["level"][0]["in_ch"] = 2
+    with pytest.raises(idf.IdfError) as e:
+        idf.World(0, st, [None] * len(st["level"]))
+    assert e.value.status == idf.IDF_EINVAL
+
+
+def test_world_create_accepts_a_single_level_low_band_setup():
+    # the valid form passes validation; without a GPU it stops at the device
+    # call (IDF_ECUDA), with one it creates the world
+    import numpy as np
+    idf = _lib()
+    st = synth.config4_stack(np.zeros((8, 8), dtype=np.float32), test_denoiser=1)
+    try:
+        idf.World(0, st, [None]).close()
+    except idf.IdfError as e:
+        assert e.status == idf.IDF_ECUDA
