@@ -425,7 +425,38 @@ template <> struct Pack8<bf16> {
 // x holds C channels of a tensor whose groups are Cg channels wide; its
 // channel c is channel c + coff of that tensor (coff > 0: the second part of
 // a concat normalised with the concat's statistics).
-template <typename TA, bool SILU>
+// 256-bit global accesses of 8 floats (the address must be 32-byte aligned;
+// callers check the base pointers on the host): one instruction where two
+// 128-bit ones would be needed, which relieves the load/store queue of the
+// memory-bound apply passes.
+__device__ __forceinline__ void ld8f(const float* p, float (&v)[8]) {
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void st8f(float* p, const float (&v)[8]) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+template <typename TA> struct Pack8W;
+template <> struct Pack8W<float> {
+  static __device__ __forceinline__ void store(float* p, const float (&v)[8]) { st8f(p, v); }
+};
+template <> struct Pack8W<tf32> {
+  static __device__ __forceinline__ void store(tf32* p, const float (&v)[8]) {
+    float r[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = tf32_rn(v[j]);
+    st8f(reinterpret_cast<float*>(p), r);
+  }
+};
+template <> struct Pack8W<bf16> {  // never instantiated with V8 (16-byte stores already)
+  static __device__ __forceinline__ void store(bf16* p, const float (&v)[8]) { Pack8<bf16>::store(p, v); }
+};
+
+// V8: 256-bit loads and stores (4-byte operand types, 32-byte aligned buffers).
+template <typename TA, bool SILU, bool V8 = false>
 __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict__ x,
                                                         const float2* __restrict__ stats,
                                                         int n_units, int units_per_win, int C,
@@ -438,9 +469,15 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
     const int b = u / units_per_win;
     const int c0 = (u % C8) * 8;
     const float2 ms = stats[b * G + (c0 + coff) / Cg];
-    const float4* src = reinterpret_cast<const float4*>(x + (int64_t)u * 8);
-    const float4 a = src[0], bq = src[1];
-    float xv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+    float xv[8];
+    if constexpr (V8) {
+      ld8f(x + (int64_t)u * 8, xv);
+    } else {
+      const float4* src = reinterpret_cast<const float4*>(x + (int64_t)u * 8);
+      const float4 a = src[0], bq = src[1];
+      xv[0] = a.x; xv[1] = a.y; xv[2] = a.z; xv[3] = a.w;
+      xv[4] = bq.x; xv[5] = bq.y; xv[6] = bq.z; xv[7] = bq.w;
+    }
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -448,8 +485,13 @@ __global__ void __launch_bounds__(256) gn_apply8_kernel(const float* __restrict_
       if (SILU) z = silu_fast(z);
       v[j] = z;
     }
-    Pack8<TA>::store(y + (int64_t)u * 8, v);
-    if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+    if constexpr (V8) {
+      Pack8W<TA>::store(y + (int64_t)u * 8, v);
+      if (copy) Pack8W<TA>::store(copy + (int64_t)u * 8, xv);
+    } else {
+      Pack8<TA>::store(y + (int64_t)u * 8, v);
+      if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+    }
     if (ylo) {
       // low parts: what bfloat16 rounding of the high parts left out
       float r[8], rc[8];
@@ -599,7 +641,7 @@ __global__ void gn_finalize_cat_kernel(CatSrc src, const double2* __restrict__ p
   stats[i] = make_float2((float)(k + m1), (float)(1.0 / sqrt(var + 1e-5)));
 }
 
-template <typename TA, bool SILU>
+template <typename TA, bool SILU, bool V8 = false>
 __global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const float2* __restrict__ stats,
                                                             int n_units, int G, TA* __restrict__ y,
                                                             TA* __restrict__ copy, TA* __restrict__ ylo,
@@ -611,9 +653,15 @@ __global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const fl
     const int r = u - b * upw;
     const int p = r / C8, c0 = (r % C8) * 8;
     const float2 ms = stats[b * G + c0 / Cg];
-    const float4* srcp = reinterpret_cast<const float4*>(cat_ptr(src, b, p, c0));
-    const float4 a = srcp[0], bq = srcp[1];
-    float xv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+    float xv[8];
+    if constexpr (V8) {
+      ld8f(cat_ptr(src, b, p, c0), xv);
+    } else {
+      const float4* srcp = reinterpret_cast<const float4*>(cat_ptr(src, b, p, c0));
+      const float4 a = srcp[0], bq = srcp[1];
+      xv[0] = a.x; xv[1] = a.y; xv[2] = a.z; xv[3] = a.w;
+      xv[4] = bq.x; xv[5] = bq.y; xv[6] = bq.z; xv[7] = bq.w;
+    }
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -621,8 +669,13 @@ __global__ void __launch_bounds__(256) gn_apply8_cat_kernel(CatSrc src, const fl
       if (SILU) z = silu_fast(z);
       v[j] = z;
     }
-    Pack8<TA>::store(y + (int64_t)u * 8, v);
-    if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+    if constexpr (V8) {
+      Pack8W<TA>::store(y + (int64_t)u * 8, v);
+      if (copy) Pack8W<TA>::store(copy + (int64_t)u * 8, xv);
+    } else {
+      Pack8<TA>::store(y + (int64_t)u * 8, v);
+      if (copy) Pack8<TA>::store(copy + (int64_t)u * 8, xv);
+    }
     if (ylo) {
       float rr[8], rc[8];
 #pragma unroll
@@ -1990,6 +2043,16 @@ void gn_apply_launch(Ctx& c, const float* x, int HW, int C, bool silu, void* y, 
   if (Cg == 0) Cg = C / G;
   const int64_t units = (int64_t)c.n * HW * (C / 8);
   const int upw = HW * (C / 8);
+  if constexpr (sizeof(TA) == 4) {
+    // 256-bit accesses when every base is 32-byte aligned (units are 8 floats)
+    if (((uintptr_t)x | (uintptr_t)y | (uintptr_t)copy) % 32 == 0 && !ylo) {
+      if (silu)
+        gn_apply8_kernel<TA, true, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, Cg, coff, (TA*)y, (TA*)copy, nullptr, nullptr);
+      else
+        gn_apply8_kernel<TA, false, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, Cg, coff, (TA*)y, (TA*)copy, nullptr, nullptr);
+      return;
+    }
+  }
   if (silu)
     gn_apply8_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(x, c.u->stats, (int)units, upw, C, G, Cg, coff, (TA*)y, (TA*)copy, (TA*)ylo, (TA*)copylo);
   else
@@ -2118,6 +2181,15 @@ template <typename TA>
 void gn_apply_cat_launch(Ctx& c, const CatSrc& src, void* y, void* copy, void* ylo, void* copylo) {
   const int G = c.u->d.groups, C = src.Ca + src.Cb, HW = src.H * src.H;
   const int64_t units = (int64_t)c.n * HW * (C / 8);
+  if constexpr (sizeof(TA) == 4) {
+    // 256-bit accesses: every source pixel starts at a multiple of 8 floats
+    // (Ca, Cb multiples of 8), so aligned bases suffice
+    if (((uintptr_t)src.a | (uintptr_t)src.b | (uintptr_t)y | (uintptr_t)copy) % 32 == 0 && !ylo) {
+      gn_apply8_cat_kernel<TA, true, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G,
+                                                                                 (TA*)y, (TA*)copy, nullptr, nullptr);
+      return;
+    }
+  }
   gn_apply8_cat_kernel<TA, true><<<grid1d(units, 256), 256, 0, c.st>>>(src, c.u->stats, (int)units, G, (TA*)y,
                                                                        (TA*)copy, (TA*)ylo, (TA*)copylo);
 }
