@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -70,6 +71,8 @@ def parse():
                    help="Earth-scale mode: an N x N metres query on the 16-channel stack with a 2048^2 fBm low band")
     p.add_argument("--profile-unet", type=int, default=0,
                    help="profiling mode: one warm-up and one timed fine-level UNet forward on N windows")
+    p.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                   help="where the nvidia-smi clock samples of the timed region are written")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp32", action="store_true")
@@ -337,8 +340,7 @@ def run_idf(args, rank, world, local):
         step(i)
     torch.cuda.synchronize()
     s0 = W.stats()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/idf_clocks_{rank}.csv")
+    clocks = Clocks(os.path.join(args.clocks_dir, f"idf_clocks_rank{rank}.csv"))
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -776,8 +778,7 @@ def run_earth(args):
         step(i)
     torch.cuda.synchronize()
     s0 = W.stats()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_earth.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/idf_clocks_earth.csv")
+    clocks = Clocks(os.path.join(args.clocks_dir, "idf_clocks_earth.csv"))
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
