@@ -53,3 +53,20 @@ def test_cone_counts_bounded_independent_of_location():
         ref = ref or c
         assert c == ref
         assert sum(c) <= 9 + 9 ** 2 + 9 ** 3 + 9 ** 4
+
+
+def test_stride_overhead_matches_the_paper():
+    # Over a large region the windows kappa selects cover every pixel
+    # (H / s)^2 times: 4x at a 50% stride and 16/9 = 1.78x at 75%, the
+    # overheads the paper prints (tests/golden/stride_overhead.txt).
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "stride_overhead.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert rows
+    for size_s, stride_s, printed in rows:
+        size, stride, printed = int(size_s), int(stride_s), float(printed)
+        side = 1_000_000 * stride
+        lo, hi = K.kappa_1d(0, side, size, stride)
+        overhead = ((hi - lo + 1) * size / side) ** 2
+        # edge windows add O(1e-6); the paper prints two decimals
+        assert abs(overhead - printed) <= 0.005, (size, stride, overhead, printed)
