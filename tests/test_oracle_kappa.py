@@ -70,3 +70,21 @@ def test_stride_overhead_matches_the_paper():
         overhead = ((hi - lo + 1) * size / side) ** 2
         # edge windows add O(1e-6); the paper prints two decimals
         assert abs(overhead - printed) <= 0.005, (size, stride, overhead, printed)
+
+
+def test_overlap_bound_and_recursive_cost_bound():
+    # Assumption 2 / the recursive cost bound (Sec. "Constant-time cost"
+    # appendix): a window region overlaps M windows, here exactly
+    # (2 H/s - 1)^2 = 9 for H = 2s; a cold query of one window region costs
+    # at most M + M^2 + ... + M^T window evaluations (c_t <= M (1 + c_{t+1}),
+    # c_T = 0).  The lazy cone with its cache stays within that bound.
+    size, stride = 32, 16
+    rng = random.Random(3)
+    for _ in range(20):
+        i, j = rng.randint(-1000, 1000), rng.randint(-1000, 1000)
+        assert len(K.kappa(*K.window_rect(i, j, size, stride), size, stride)) == 9
+    M = 9
+    for T in (1, 2, 4, 6):
+        counts = K.cone_window_counts(*K.window_rect(5, -7, size, stride), size, stride, T)
+        bound = sum(M ** k for k in range(1, T + 1))
+        assert sum(counts) <= bound, (T, counts, bound)
