@@ -89,3 +89,41 @@ def test_conv_is_cross_correlation():
     w[0, 0, 0, 0] = 1.0
     y = U.conv(x, w)[0, 0]
     assert y[1, 1] == x[0, 0, 0, 0] and y[0, 0] == 0.0 and y[3, 3] == x[0, 0, 2, 2]
+
+
+def test_upsampled_branch_phase_identity():
+    # The identity the tensor-core path uses for decoder blocks: a 3x3
+    # convolution of [nearest-up2(a), b] equals the 3x3 convolution of b plus,
+    # for each output phase (py, px), a 2x2 convolution of a at its own
+    # resolution whose taps sum the 3x3 taps reading the same pixel of a
+    # (input rows floor((2Y + py + dy) / 2) = Y + py - 1 + ty); and the 1x1
+    # shortcut of the concat equals up2(W_a a) + W_b b.
+    rng = np.random.default_rng(11)
+    Ca, Cb, Co, h = 3, 2, 4, 5
+    a = rng.standard_normal((1, Ca, h, h))
+    b = rng.standard_normal((1, Cb, 2 * h, 2 * h))
+    w = rng.standard_normal((Co, Ca + Cb, 3, 3))
+    wsk = rng.standard_normal((Co, Ca + Cb, 1, 1))
+    cat = np.concatenate([U.up2(a), b], axis=1)
+    ref = U.conv(cat, w)
+    out = U.conv(b, w[:, Ca:])
+    ap = np.pad(a, ((0, 0), (0, 0), (1, 1), (1, 1)))
+    for py in range(2):
+        for px in range(2):
+            wp = np.zeros((Co, Ca, 2, 2))
+            for ky in range(3):
+                for kx in range(3):
+                    ty = (py + ky - 1) // 2 - (py - 1)
+                    tx = (px + kx - 1) // 2 - (px - 1)
+                    wp[:, :, ty, tx] += w[:, :Ca, ky, kx]
+            ph = np.zeros((1, Co, h, h))
+            for ty in range(2):
+                for tx in range(2):
+                    oy, ox = py - 1 + ty, px - 1 + tx
+                    ph += np.einsum("oc,bchw->bohw", wp[:, :, ty, tx],
+                                    ap[:, :, 1 + oy:1 + oy + h, 1 + ox:1 + ox + h])
+            out[:, :, py::2, px::2] += ph
+    assert np.allclose(out, ref, rtol=0, atol=1e-12)
+    sk_ref = U.conv(cat, wsk)
+    sk = U.up2(U.conv(a, wsk[:, :Ca])) + U.conv(b, wsk[:, Ca:])
+    assert np.allclose(sk, sk_ref, rtol=0, atol=1e-12)
