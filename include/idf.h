@@ -149,9 +149,16 @@ typedef struct {
 /* ---------------------------------------------------------------- worlds */
 
 /* Create a world: validates the stack, copies weights to the device (and
- * packs BF16 copies when precision = IDF_BF16), computes the sigma schedule,
- * preconditioning coefficients, blend table and blur taps in FP64 on the
- * host, and allocates the tile cache.  *out is NULL on failure. */
+ * packs the tensor-core layouts for IDF_BF16 / IDF_BF16X3 / IDF_TF32: bf16
+ * with low parts or tf32-rounded float32, plus the derived weights of the
+ * half-resolution decoder blocks), copies a low-band fixture if given,
+ * computes the sigma schedule, preconditioning coefficients, blend table and
+ * blur taps in FP64 on the host, and allocates the tile cache and the UNet
+ * arena.  Returns IDF_EINVAL for an invalid stack or options (among them a
+ * low-band fixture with two levels, without laplacian = 1 or with a level of
+ * in_ch != 1, and laplacian = 1 with one level and no fixture) before any
+ * device call, IDF_EUNSUPPORTED for IDF_FP8_E4M3, IDF_ENOMEM / IDF_ECUDA on
+ * device allocation or CUDA failures.  *out is NULL on failure. */
 idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack,
                             const idf_world_opts* opts, idf_world** out);
 
