@@ -4,9 +4,13 @@ One step = one cold query of a 4096 x 4096 heightmap in metres through the
 two-level stack (coarse UNet 64/128/128 at 1/8 resolution conditioning a fine
 UNet 64/128/256/256 with bottom attention, 128-pixel windows at stride 64, 20
 blended steps per level, Laplacian decode): noise, scheduler, window gather,
-BF16 tensor-core UNets, blend/update/re-noise and decode all run per step.
-Weights are seeded random-init (synthetic data); every step queries a fresh
-location with an emptied tile cache, so nothing is reused across steps.
+tensor-core UNets (TF32 by default), blend/update/re-noise and decode all run
+per step.  Weights are seeded random-init (synthetic data); every step
+queries a fresh location with an emptied tile cache, so nothing is reused
+across steps.  Beside the headline the run measures: the end-to-end rate
+into a host buffer, a second precision, the plain FP32 sampler on a cold
+query of the same size, and each precision's error against the FP64
+oracle's stored values of the full configuration on a 256^2 crop.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl idf|reference]
 
@@ -34,9 +38,9 @@ QUERY = 4096
 METRIC = "final heightmap px/s, BF16/FP8+batched vs plain FP32 at stated error"
 WORKLOAD = ("2-level hierarchy (coarse 64/128/128 @1/8, fine 64/128/256/256 + attention), "
             "128x128 windows stride 64, 20 steps, 4096x4096 metres query, tensor-core convs")
-# max abs error vs the FP64 oracle on the full-width stack (2 blended steps,
-# the worst case), in sigma_out, as the GPU parity tests measure it
-STATED_ERROR = {"fp32": 1.5e-5, "tf32": 4.5e-3, "bf16x3": 9.1e-5, "bf16": 3.7e-2}
+# FP64 oracle values of the full 20-step configuration on a 256^2 crop,
+# written once by tests/golden/make_config2_crop.py (oracle only)
+CROP_FIXTURE = os.path.join(ROOT, "tests", "golden", "config2_crop_k20.npz")
 
 
 def bench_config(q: int, precision: str, windows_per_step=None, world: int = 1) -> dict:
@@ -75,7 +79,8 @@ def parse():
                    help="where the nvidia-smi clock samples of the timed region are written")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-fp32", action="store_true")
+    p.add_argument("--fp32-steps", type=int, default=1,
+                   help="cold queries timed through the plain FP32 sampler (0 = skip)")
     return p.parse_args()
 
 
@@ -127,34 +132,28 @@ def stack_and_weights():
     return st, wts
 
 
-def window_counts(st, q):
-    """Windows a cold metres query of a q x q region evaluates per level
-    (cone of the decode rect; coarse cone covers the fine conditioning)."""
-    import paper_2512_08309_gb300 as idf
-    Lr, Hr = idf.laplacian_halo(st, 0, 0, q, q)
+def oracle_window_counts(st, q):
+    """Windows a cold metres query of a q x q region evaluates per level, by
+    the oracle's own geometry: the fine cone of the decode's H rect
+    (oracle.laplacian.decode_rects, oracle.kappa), and the coarse cone of
+    every coarse pixel that the fine cone's conditioning or the decode's low
+    band reads."""
+    from oracle import kappa as OK
+    from oracle import laplacian as OL
     fine, coarse = st["level"][1], st["level"][0]
-
-    def cone(x0, y0, w, h, lv):
-        s, H, K = lv["stride"], lv["window"], lv["steps"]
-        r = H // s
-        ty0, tx0 = y0 // s, x0 // s
-        ty1, tx1 = (y0 + h - 1) // s, (x0 + w - 1) // s
-        n = 0
-        wins = None
-        for _ in range(K):
-            wy0, wx0, wy1, wx1 = ty0 - (r - 1), tx0 - (r - 1), ty1, tx1
-            n += (wy1 - wy0 + 1) * (wx1 - wx0 + 1)
-            wins = (wy0, wx0, wy1, wx1)
-            ty0, tx0, ty1, tx1 = wy0, wx0, wy1 + r - 1, wx1 + r - 1
-        return n, wins
-
-    nf, wins = cone(Hr[0], Hr[1], Hr[2], Hr[3], fine)
-    s, H, f = fine["stride"], fine["window"], fine["scale_to_parent"]
-    cy0, cx0 = (wins[0] * s) // f, (wins[1] * s) // f
-    cy1, cx1 = (wins[2] * s + H - 1) // f, (wins[3] * s + H - 1) // f
-    y0, x0 = min(cy0, Lr[1]), min(cx0, Lr[0])
-    y1, x1 = max(cy1, Lr[1] + Lr[3] - 1), max(cx1, Lr[0] + Lr[2] - 1)
-    nc, _ = cone(x0, y0, x1 - x0 + 1, y1 - y0 + 1, coarse)
+    (ly0, lx0, lh, lw), (hy0, hx0, hh, hw) = OL.decode_rects(0, 0, q, q, factor=st["lap_factor"],
+                                                             radius=st["lap_radius"])
+    H, s, K = fine["window"], fine["stride"], fine["steps"]
+    nf = sum(OK.cone_window_counts(hy0, hx0, hh, hw, H, s, K))
+    y0, x0, h, w = hy0, hx0, hh, hw
+    for _ in range(K):
+        ri, rj = OK.kappa_1d(y0, y0 + h, H, s), OK.kappa_1d(x0, x0 + w, H, s)
+        y0, x0, h, w = ri[0] * s, rj[0] * s, (ri[1] - ri[0]) * s + H, (rj[1] - rj[0]) * s + H
+    f = fine["scale_to_parent"]
+    cy0, cx0 = min(y0 // f, ly0), min(x0 // f, lx0)
+    cy1, cx1 = max((y0 + h - 1) // f, ly0 + lh - 1), max((x0 + w - 1) // f, lx0 + lw - 1)
+    nc = sum(OK.cone_window_counts(cy0, cx0, cy1 - cy0 + 1, cx1 - cx0 + 1, coarse["window"],
+                                   coarse["stride"], coarse["steps"]))
     return nf, nc
 
 
@@ -219,7 +218,7 @@ def oracle_sample(seconds=15.0):
     from oracle import unet as OU
     st = synth.config2_stack()
     wts = [synth.weights([s for _, s in OU.param_shapes(lv)], 0, i) for i, lv in enumerate(st["level"])]
-    nf, nc = window_counts(st, QUERY)
+    nf, nc = oracle_window_counts(st, QUERY)
     world = OS.World(0, st, wts)
     fine, coarse = world.levels[1], world.levels[0]
     # coarse result the fine conditioning reads: a constant stand-in avoids
@@ -252,8 +251,9 @@ def oracle_sample(seconds=15.0):
         est = tf / done_f * nf + tc / done_c * nc
     px_s = QUERY * QUERY / est
     desc = (f"FP64 NumPy oracle: {done_f} fine + {done_c} coarse 128x128 window evaluations "
-            f"in {dt:.1f} s, scaled to the {nf} fine + {nc} coarse windows of one cold "
-            f"{QUERY}x{QUERY} query")
+            f"(preconditioned UNet + re-noise; the fine level's conditioning read replaced by "
+            f"zeros) in {dt:.1f} s, extrapolated to the {nf} fine + {nc} coarse windows of one "
+            f"cold {QUERY}x{QUERY} query (oracle kappa cone)")
     threads = os.cpu_count()
     return px_s, desc, threads, est
 
@@ -281,6 +281,8 @@ def run_reference(args, rank, world):
         "data": "synthetic", "config": bench_config(QUERY, args.precision),
         "cpu_baseline": {"value": v, "unit": "px/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "ms_per_step_kind": "extrapolated: each step times a bounded sample of the query's window "
+                            "evaluations and scales it to the whole cone",
         "wall_s": elapsed,
     }
     print(json.dumps(line))
@@ -311,6 +313,65 @@ def peaks():
         d = json.load(open(p))
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def crop_error(idf, W):
+    """Error of world W against the stored FP64 oracle values of the full
+    20-step configuration on its 256^2 crop: max |model - oracle| in
+    sigma_out and max |metres - oracle| in metres, measured now."""
+    import numpy as np
+    if not os.path.exists(CROP_FIXTURE):
+        return {"unavailable": "oracle fixture missing"}
+    d = np.load(CROP_FIXTURE)
+    x0, y0, w, h = (int(v) for v in d["crop"])
+    m = W.query(x0, y0, w, h).astype(np.float64)
+    v = W.query(x0, y0, w, h, kind=idf.IDF_OUT_METRES).astype(np.float64)
+    em = float(np.max(np.abs(m - d["model"].astype(np.float64))))
+    ev = float(np.max(np.abs(v - d["metres"].astype(np.float64))))
+    return {"model_max_abs_sigma_out": em / float(d["sigma_model"]), "metres_max_abs_m": ev,
+            "metres_abs_max_in_crop": float(np.max(np.abs(d["metres"]))),
+            "crop": [x0, y0, w, h], "steps": int(d["steps"]),
+            "against": "FP64 oracle (Eq. 1 over the crop's whole cone), tests/golden/config2_crop_k20.npz"}
+
+
+def tf32_peak(dev, seconds=4.0):
+    """cuBLAS TF32 GEMM (float32 8192^3 with TF32 tensor cores) back to back
+    for `seconds`: the measured dense TF32 rate of this GPU, TFLOP/s."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn((n, n), device=dev)
+        b = torch.randn((n, n), device=dev)
+        c = torch.empty((n, n), device=dev)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        burst = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            burst = max(burst, 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1000.0) / 1e12)
+        it = 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        while time.perf_counter() - t0 < seconds:
+            for _ in range(10):
+                torch.matmul(a, b, out=c)
+            it += 10
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        sustained = 2.0 * n ** 3 * it / (e0.elapsed_time(e1) / 1000.0) / 1e12
+        del a, b, c
+        return burst, sustained
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def run_idf(args, rank, world, local):
@@ -370,13 +431,16 @@ def run_idf(args, rank, world, local):
     pk, pk_kind = peaks()
     tc = prof["conv_tc"]
     achieved = tc["flops"] / (tc["ms"] / 1000.0) / 1e12 if tc["ms"] > 0 else 0.0
-    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-    peak_kind = f"{pk_kind} bf16 sustained"
+    bf16_sus = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    # the contraction's own dtype: TF32 is measured here (cuBLAS TF32 GEMM,
+    # sustained, as conv_tc runs inside a seconds-long step); the nominal
+    # ratio (1.1 / 2.25 PFLOP/s dense) x the measured bf16 peak is given beside it
+    tf32_burst, tf32_sus = tf32_peak(dev) if "tf32" in (args.precision, args.also) else (None, None)
+    peak = bf16_sus
+    peak_kind = f"{pk_kind} bf16 sustained (MEASURED_PEAKS.json)"
     if args.precision == "tf32":
-        # the contraction's own dtype: the measured bf16 peak x the nominal
-        # dense tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
-        peak = peak * 1.1 / 2.25
-        peak_kind = f"{pk_kind} bf16 sustained x 1.1/2.25 (tf32)"
+        peak = tf32_sus
+        peak_kind = "measured here: cuBLAS TF32 GEMM 8192^3, sustained over 4 s"
     rec = traffic_record(args.precision)
     fpl = tc["flops"] / max(1, tc["launches"])
     # bf16x3 issues three bf16 products per multiply-add of the convolution
@@ -391,6 +455,9 @@ def run_idf(args, rank, world, local):
                 "traffic": rec["dram_bytes_per_algorithmic_flop"] * fpl if rec else None,
                 "algorithmic_bytes_per_launch": tc["bytes"] / max(1, tc["launches"]),
                 "flops_per_launch": tc["flops"] / max(1, tc["launches"]),
+                "tf32_peak_measured": {"burst": tf32_burst, "sustained": tf32_sus} if tf32_sus else None,
+                "frac_vs_nominal_ratio": (achieved / (bf16_sus * 1.1 / 2.25)) if args.precision == "tf32"
+                else None,
                 "avg_launch_ms": tc["ms"] / max(1, tc["launches"]),
                 "share_of_step": tc["ms"] / ms if ms > 0 else None}
     hbm = {}
@@ -446,8 +513,8 @@ def run_idf(args, rank, world, local):
         dt = max_over_ranks(time.perf_counter() - t0, world)
         line["e2e"] = {"value": world * q * q * n_e2e / dt, "unit": "px/s", "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": q * q * 4, "steps": n_e2e}
+    line["error_vs_oracle"] = crop_error(idf, W) if rank == 0 else None
     W.close()
-    line["error_vs_oracle_sigma_out"] = STATED_ERROR.get(args.precision)
 
     # a second precision (by default the compensated three-product bf16
     # path) on the same workload, timed the same way, beside the headline
@@ -461,65 +528,63 @@ def run_idf(args, rank, world, local):
             x0, y0 = loc(2000 + i)
             W2.query_device(x0, y0, q, q, out.data_ptr(), q, kind=idf.IDF_OUT_METRES, stream=stream)
 
-        for i in range(args.warmup):
+        # the second precision is context beside the headline: at most 3
+        # warm-up and 5 timed steps
+        w2n, k2n = min(args.warmup, 3), min(args.steps, 5)
+        for i in range(w2n):
             step2(i)
         torch.cuda.synchronize()
         t0 = W2.stats()
         barrier(world)
         torch.cuda.synchronize()
         e0.record(stream)
-        for i in range(args.steps):
-            step2(args.warmup + i)
+        for i in range(k2n):
+            step2(w2n + i)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
         ms2 = max_over_ranks(e0.elapsed_time(e1), world)
         t1 = W2.stats()
+        err2 = crop_error(idf, W2) if rank == 0 else None
         W2.close()
         c0, c1 = t0["profile"]["conv_tc"], t1["profile"]["conv_tc"]
         tc_ms = c1["ms"] - c0["ms"]
         ach = (c1["flops"] - c0["flops"]) / (tc_ms / 1000.0) / 1e12 if tc_ms > 0 else 0.0
-        pk2 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * (1.1 / 2.25 if args.also == "tf32" else 1.0)
+        pk2 = tf32_sus if args.also == "tf32" else bf16_sus
         mf2 = 3.0 if args.also == "bf16x3" else 1.0
         line["also"] = {args.also: {
-            "value": world * q * q * args.steps / (ms2 / 1000.0), "unit": "px/s", "ms_per_step": ms2 / args.steps,
-            "error_vs_oracle_sigma_out": STATED_ERROR.get(args.also),
+            "value": world * q * q * k2n / (ms2 / 1000.0), "unit": "px/s", "ms_per_step": ms2 / k2n,
+            "steps": k2n, "warmup": w2n, "error_vs_oracle": err2,
             "conv_tc_achieved_tflops": ach, "conv_tc_frac": ach / pk2, "mma_work_factor": mf2,
             "conv_tc_frac_mma": ach * mf2 / pk2, "conv_tc_share_of_step": tc_ms / ms2 if ms2 > 0 else None}}
 
-    # the plain FP32 sampler's network and the BF16 one, windows/s through
-    # idf_unet_forward, converted to this workload's px/s (UNets dominate)
-    if not args.no_fp32 and rank == 0:
-        nf, nc = window_counts(st, q)
-        res = {}
-        for prec, nb in (("fp32", 8), ("bf16", 64), ("bf16x3", 64), ("tf32", 64)):
-            Wp = idf.World(0, st, wts, precision=prec, max_batch=nb)
-            t_lv = []
-            for li, n_win in ((1, nb), (0, nb)):
-                H = st["level"][li]["window"]
-                x = torch.randn((n_win, st["level"][li]["in_ch"], H, H), device=dev)
-                y = torch.empty((n_win, 1, H, H), device=dev)
-                Wp.unet_forward(li, x.data_ptr(), n_win, y.data_ptr(), stream=stream)
-                torch.cuda.synchronize()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                Wp.unet_forward(li, x.data_ptr(), n_win, y.data_ptr(), stream=stream)
-                b.record(stream)
-                torch.cuda.synchronize()
-                t_lv.append(a.elapsed_time(b) / 1000.0 / n_win)
-            Wp.close()
-            t_query = t_lv[0] * nf + t_lv[1] * nc
-            res[prec] = {"px_s": q * q / t_query, "fine_window_ms": 1000 * t_lv[0],
-                         "coarse_window_ms": 1000 * t_lv[1], "batch": nb}
-        line["plain_fp32"] = {"value": res["fp32"]["px_s"], "unit": "px/s",
-                              "method": "FP32 SIMT UNet windows/s (idf_unet_forward) x windows per "
-                                        "final px of this workload",
-                              "bf16_same_method": res["bf16"]["px_s"],
-                              "bf16x3_same_method": res["bf16x3"]["px_s"],
-                              "tf32_same_method": res["tf32"]["px_s"],
-                              "speedup_bf16_vs_fp32_unet": res["bf16"]["px_s"] / res["fp32"]["px_s"],
-                              "speedup_bf16x3_vs_fp32_unet": res["bf16x3"]["px_s"] / res["fp32"]["px_s"],
-                              "detail": res}
+    # the plain FP32 sampler (float32 SIMT convolutions, same algorithm, one
+    # query at a time): one cold q x q metres query at a fresh location,
+    # timed the same way, after a small warm-up query
+    if args.fp32_steps > 0 and rank == 0:
+        Wp = idf.World(0, st, wts, precision="fp32", device=local,
+                       workspace_bytes=int(args.workspace_gb * (1 << 30)),
+                       cache_bytes=int(args.cache_gb * (1 << 30)))
+        wq = torch.empty((256, 256), dtype=torch.float32, device=dev)
+        Wp.query_device(*loc(3000), 256, 256, wq.data_ptr(), 256, kind=idf.IDF_OUT_METRES, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.fp32_steps):
+            Wp.cache_clear()
+            x0, y0 = loc(3001 + i)
+            Wp.query_device(x0, y0, q, q, out.data_ptr(), q, kind=idf.IDF_OUT_METRES, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msp = e0.elapsed_time(e1)
+        Wp.close()
+        fp32_pxs = q * q * args.fp32_steps / (msp / 1000.0)
+        line["plain_fp32"] = {"value": fp32_pxs, "unit": "px/s", "ms_per_step": msp / args.fp32_steps,
+                              "steps": args.fp32_steps,
+                              "method": "measured: cold metres query of the same size at a fresh location "
+                                        "through an IDF_FP32 world (float32 SIMT convolutions)",
+                              f"speedup_{args.precision}": value / fp32_pxs}
+        if "also" in line:
+            line["plain_fp32"][f"speedup_{args.also}"] = line["also"][args.also]["value"] / fp32_pxs
     if not args.no_cpu and rank == 0 and world == 1:
         px, desc, threads, est = oracle_sample(seconds=15.0)
         line["cpu_baseline"] = {"value": px, "unit": "px/s", "cores": threads, "kind": "oracle",

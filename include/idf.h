@@ -205,6 +205,25 @@ idf_status idf_debug_cone(idf_world* world, int64_t x0, int64_t y0, int32_t w, i
                           int32_t level, int32_t step, int64_t* win_ij, int32_t cap,
                           int32_t* n_out);
 
+/* Test-only: the tile keys (tile row, tile column) of J_step held in a
+ * level's cache (step 1..K; J_0 is the noise and is never cached), sorted
+ * by row then column.  Writes up to cap pairs into ty_tx and the total count
+ * into *n_out.  Reads host bookkeeping only (Sec. 3.3: the processed set P
+ * of the lazy algorithm, kept here as finalized tiles). */
+idf_status idf_debug_cache_keys(idf_world* world, int32_t level, int32_t step, int32_t* ty_tx,
+                                int32_t cap, int32_t* n_out);
+
+/* Test-only failure injection from the host: after synchronizing the
+ * world's stream, writes `value` into a device status word -- which = 0:
+ * the word the tensor-core convolutions set when a bounded wait runs out
+ * (read back as IDF_ETIMEOUT by the next synchronizing query, which also
+ * makes every later tensor-core launch return at once); which = 1: the
+ * conditioning gather's bounds-check flag (read back as IDF_EDEVICE_CHECK
+ * and cleared).  No kernel faults or waits; the failure paths that follow
+ * are the same as for a real expiry or bounds violation.  IDF_EINVAL for
+ * another `which`. */
+idf_status idf_debug_set_status(idf_world* world, int32_t which, int32_t value);
+
 /* --------------------------------------------------------- building blocks */
 
 /* The seed function G (App. B): N(seed, level, step, x, y), standard normal

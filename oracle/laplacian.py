@@ -98,6 +98,24 @@ def blur2d_valid(D: np.ndarray, g: np.ndarray) -> np.ndarray:
     return out
 
 
+def decode_rects(y0, x0, h, w, *, factor=8, radius=15):
+    """The rects (y0, x0, h, w) of L (coarse grid) and of H (fine grid) that
+    the decode of the fine rect reads: the coarse range of L^ read by the
+    final upsampling, grown by the blur radius, is D = down(P) over its
+    aligned fine blocks, and P there reads L through one more upsampling."""
+    f = int(factor)
+    R = int(radius)
+    qy0, qy1 = up_range(y0, h, f)
+    qx0, qx1 = up_range(x0, w, f)
+    dy0, dy1 = qy0 - R, qy1 + R
+    dx0, dx1 = qx0 - R, qx1 + R
+    py0, px0 = f * dy0, f * dx0
+    ph, pw = f * (dy1 - dy0 + 1), f * (dx1 - dx0 + 1)
+    ly0, ly1 = up_range(py0, ph, f)
+    lx0, lx1 = up_range(px0, pw, f)
+    return (ly0, lx0, ly1 - ly0 + 1, lx1 - lx0 + 1), (py0, px0, ph, pw)
+
+
 def decode_signed(Lfun, Hfun, y0, x0, h, w, *, factor=8, blur_sigma=5.0, radius=15,
                   low_mu=0.0, low_scale=50.0, res_scale=1.5):
     """v = up(L^) + H over the fine rect (signed-sqrt units).
@@ -107,17 +125,11 @@ def decode_signed(Lfun, Hfun, y0, x0, h, w, *, factor=8, blur_sigma=5.0, radius=
     f = int(factor)
     R = int(radius)
     g = blur_taps(blur_sigma, R)
+    (ly0, lx0, lh, lw), (py0, px0, ph, pw) = decode_rects(y0, x0, h, w, factor=f, radius=R)
     # coarse rows/cols of L^ the final upsampling reads
     qy0, qy1 = up_range(y0, h, f)
     qx0, qx1 = up_range(x0, w, f)
-    # D = down(P) over that range +- R
-    dy0, dy1 = qy0 - R, qy1 + R
-    dx0, dx1 = qx0 - R, qx1 + R
-    py0, px0 = f * dy0, f * dx0
-    ph, pw = f * (dy1 - dy0 + 1), f * (dx1 - dx0 + 1)
-    ly0, ly1 = up_range(py0, ph, f)
-    lx0, lx1 = up_range(px0, pw, f)
-    l = low_mu + low_scale * np.asarray(Lfun(ly0, lx0, ly1 - ly0 + 1, lx1 - lx0 + 1), dtype=np.float64)
+    l = low_mu + low_scale * np.asarray(Lfun(ly0, lx0, lh, lw), dtype=np.float64)
     hP = res_scale * np.asarray(Hfun(py0, px0, ph, pw), dtype=np.float64)
     P = up_bilinear(l, ly0, lx0, py0, px0, ph, pw, f) + hP
     D = down_mean(P, f)

@@ -62,6 +62,7 @@ class _LevelCommon:
         self.parent = parent
         self.scale = int(lv.get("scale_to_parent", 0))
         self.phi_calls = 0
+        self.fmap = None      # optional xin -> F over a batch (oracle.parallel); same values
 
     def noise(self, step, y0, x0, h, w):
         return N_.normal_region(self.seed, self.level_index, step, x0, y0, w, h).astype(np.float64)
@@ -84,9 +85,12 @@ class _LevelCommon:
             chans.append(np.stack([self.cond(*r) for r in rects])[:, None])
         xin = np.concatenate(chans, axis=1)
         F = np.empty((len(xs), self.H, self.H))
-        bs = 64 if self.H <= 32 else 1
-        for b0 in range(0, len(xs), bs):
-            F[b0:b0 + bs] = U_.forward(self.lv, self.params, xin[b0:b0 + bs])[:, 0]
+        if self.fmap is not None and self.params is not None:
+            F[:] = self.fmap(xin)
+        else:
+            bs = 64 if self.H <= 32 else 1
+            for b0 in range(0, len(xs), bs):
+                F[b0:b0 + bs] = U_.forward(self.lv, self.params, xin[b0:b0 + bs])[:, 0]
         self.phi_calls += len(xs)
         out = []
         for x, r, f in zip(xs, rects, F):
@@ -242,3 +246,58 @@ def eager_world_model(seed: int, stack: dict, weights: list, y0, x0, h, w):
     coarse.run(qy0, qx0, qy1 - qy0 + 1, qx1 - qx0 + 1)
     fine.parent = coarse
     return fine.run(y0, x0, h, w)
+
+
+class EagerWorld:
+    """Eq. 1 brute force for a model stack over one region, grown by the
+    Laplacian decode's halo when metres are wanted (App. C.3 chaining: the
+    coarse level runs eagerly over every coarse pixel that the fine cone's
+    conditioning or the decode's low band reads).  ``fmap`` optionally
+    supplies a batch evaluator of F per level (oracle.parallel)."""
+
+    def __init__(self, seed: int, stack: dict, weights: list, y0, x0, h, w, *,
+                 metres: bool = False, fmap=None):
+        from . import laplacian as L_
+        lvls = stack["level"]
+        eps = stack.get("blend_eps", 1e-3)
+        self.stack = stack
+        mk = lambda li, parent=None: EagerLevel(seed, lvls[li], li,
+                                                weights=weights[li] if weights else None,
+                                                blend_eps=eps, parent=parent)
+        rect = (y0, x0, h, w)
+        lrect = None
+        if metres:
+            (ly0, lx0, lh, lw), rect = L_.decode_rects(y0, x0, h, w, factor=stack["lap_factor"],
+                                                        radius=stack["lap_radius"])
+            lrect = (ly0, lx0, lh, lw)
+        self.fine = mk(len(lvls) - 1)
+        self.coarse = None
+        if len(lvls) == 2:
+            f = int(lvls[1]["scale_to_parent"])
+            cy, cx, ch, cw = cone_rects(self.fine, *rect)[0]
+            qy0, qx0 = cy // f, cx // f
+            qy1, qx1 = (cy + ch - 1) // f, (cx + cw - 1) // f
+            if lrect is not None:
+                qy0, qx0 = min(qy0, lrect[0]), min(qx0, lrect[1])
+                qy1, qx1 = max(qy1, lrect[0] + lrect[2] - 1), max(qx1, lrect[1] + lrect[3] - 1)
+            self.coarse = mk(0)
+            if fmap is not None:
+                self.coarse.fmap = fmap(0)
+            self.coarse.run(qy0, qx0, qy1 - qy0 + 1, qx1 - qx0 + 1)
+            self.fine.parent = self.coarse
+        if fmap is not None:
+            self.fine.fmap = fmap(len(lvls) - 1)
+        self.fine.run(*rect)
+
+    def model(self, y0, x0, h, w):
+        return self.fine.final(y0, x0, h, w)
+
+    def metres(self, y0, x0, h, w):
+        from . import laplacian as L_
+        st = self.stack
+        fx = st.get("low_band_fixture")
+        lfun = L_.periodic_lowband(fx) if fx is not None else self.coarse.final
+        return L_.decode_metres(lfun, self.fine.final, y0, x0, h, w,
+                                factor=st["lap_factor"], blur_sigma=st["lap_blur_sigma"],
+                                radius=st["lap_radius"], low_mu=st["low_mu"],
+                                low_scale=st["low_scale"], res_scale=st["res_scale"])

@@ -28,7 +28,8 @@ PRECISIONS = {"fp32": IDF_FP32, "bf16": IDF_BF16, "fp8": IDF_FP8_E4M3, "bf16x3":
 EXPORTS = [
     "idf_world_create", "idf_world_query", "idf_world_query_device", "idf_world_query_batch",
     "idf_world_cache_clear", "idf_world_stats", "idf_world_last_error", "idf_world_destroy",
-    "idf_debug_cone", "idf_noise_fill", "idf_model_param_count", "idf_model_param_shape",
+    "idf_debug_cone", "idf_debug_cache_keys", "idf_debug_set_status", "idf_noise_fill",
+    "idf_model_param_count", "idf_model_param_shape",
     "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo", "idf_laplacian_decode_noalloc",
     "idf_student_create", "idf_student_loss_grad", "idf_student_adamw", "idf_student_zero_grad",
     "idf_student_read", "idf_student_last_error", "idf_student_destroy",
@@ -100,6 +101,8 @@ def lib():
         "idf_world_last_error": ([vp], C.c_char_p),
         "idf_world_destroy": ([vp], None),
         "idf_debug_cone": ([vp, i64, i64, i32, i32, i32, i32, C.POINTER(i64), i32, C.POINTER(i32)], i32),
+        "idf_debug_cache_keys": ([vp, i32, i32, C.POINTER(i32), i32, C.POINTER(i32)], i32),
+        "idf_debug_set_status": ([vp, i32, i32], i32),
         "idf_noise_fill": ([u64, u32, u32, i64, i64, i32, i32, vp, i64, vp], i32),
         "idf_model_param_count": ([C.POINTER(idf_level_desc), C.POINTER(i32), C.POINTER(C.c_size_t)], i32),
         "idf_model_param_shape": ([C.POINTER(idf_level_desc), i32, C.POINTER(i32)], i32),
@@ -292,6 +295,20 @@ class World:
         _check(lib().idf_debug_cone(self._h, x0, y0, w, h, level, step, buf, n.value, C.byref(n)),
                "idf_debug_cone", self._h)
         return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+    def debug_cache_keys(self, level: int, step: int):
+        """Sorted (tile row, tile column) keys of J_step cached for a level."""
+        n = C.c_int32()
+        _check(lib().idf_debug_cache_keys(self._h, level, step, None, 0, C.byref(n)),
+               "idf_debug_cache_keys", self._h)
+        buf = (C.c_int32 * (2 * max(1, n.value)))()
+        _check(lib().idf_debug_cache_keys(self._h, level, step, buf, n.value, C.byref(n)),
+               "idf_debug_cache_keys", self._h)
+        return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+    def debug_set_status(self, which: int, value: int):
+        """Host-side failure injection into a device status word (test only)."""
+        _check(lib().idf_debug_set_status(self._h, which, value), "idf_debug_set_status", self._h)
 
     def unet_forward(self, level: int, x_ptr: int, n: int, y_ptr: int, stream=None):
         _check(lib().idf_unet_forward(self._h, level, C.c_void_p(x_ptr), n, C.c_void_p(y_ptr),

@@ -1914,9 +1914,11 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
   const double flops = 2.0 * c.n * H * W * (double)w.cout * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0));
   if (tc_path<TA>(w, H) && !x_f32) {
     std::string e;
-    // algorithmic bytes: bf16 operands read once, weights, float32 output (+ residual)
-    const double by = c.n * H * W * (2.0 * (w.cin + (w2 ? w2->cin : 0)) + 4.0 * w.cout * (res ? 2 : 1)) +
-                      2.0 * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0)) * w.cout;
+    // algorithmic bytes: operands read once at their own width (2 B bf16;
+    // 4 B tf32 or bf16 hi + lo), weights likewise, float32 output (+ residual)
+    const double ob = (std::is_same<TA, tf32>::value || c.u->split) ? 4.0 : 2.0;
+    const double by = c.n * H * W * (ob * (w.cin + (w2 ? w2->cin : 0)) + 4.0 * w.cout * (res ? 2 : 1)) +
+                      ob * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0)) * w.cout;
     const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
     const bool sp = c.u->split;
     const bool tf = std::is_same<TA, tf32>::value;

@@ -1096,6 +1096,41 @@ idf_status idf_debug_cone(idf_world* W, int64_t x0, int64_t y0, int32_t w, int32
   return IDF_OK;
 }
 
+idf_status idf_debug_cache_keys(idf_world* W, int32_t level, int32_t step, int32_t* ty_tx, int32_t cap,
+                                int32_t* n_out) {
+  if (!W || !n_out) return IDF_EINVAL;
+  if (level < 0 || level >= (int)W->lv.size()) return fail(W, IDF_EINVAL, "bad level");
+  Level& L = W->lv[level];
+  if (step < 1 || step > L.K) return fail(W, IDF_EINVAL, "bad step");
+  std::vector<uint64_t> keys;
+  keys.reserve(L.cache.map[step].size());
+  for (auto& kv : L.cache.map[step]) keys.push_back(kv.first);
+  std::sort(keys.begin(), keys.end(), [](uint64_t a, uint64_t b) {
+    return khi(a) != khi(b) ? khi(a) < khi(b) : klo(a) < klo(b);
+  });
+  *n_out = (int32_t)keys.size();
+  if (ty_tx)
+    for (int32_t i = 0; i < std::min(*n_out, cap); ++i) {
+      ty_tx[2 * i] = khi(keys[i]);
+      ty_tx[2 * i + 1] = klo(keys[i]);
+    }
+  return IDF_OK;
+}
+
+idf_status idf_debug_set_status(idf_world* W, int32_t which, int32_t value) {
+  if (!W || which < 0 || which > 1) return IDF_EINVAL;
+  if (!cuda_ok(W, cudaStreamSynchronize(W->st), "sync")) return fail(W, IDF_ECUDA, W->last_error);
+  if (which == 0) {
+    for (auto& L : W->lv)
+      if (L.unet && !cuda_ok(W, cudaMemcpy(unet_status(L.unet), &value, sizeof(int), cudaMemcpyHostToDevice),
+                             "write status"))
+        return fail(W, IDF_ECUDA, W->last_error);
+  } else if (!cuda_ok(W, cudaMemcpy(W->d_err, &value, sizeof(int), cudaMemcpyHostToDevice), "write status")) {
+    return fail(W, IDF_ECUDA, W->last_error);
+  }
+  return IDF_OK;
+}
+
 idf_status idf_noise_fill(uint64_t seed, uint32_t level, uint32_t step, int64_t x0, int64_t y0,
                           int32_t w, int32_t h, float* out_dev, int64_t pitch, void* stream) {
   if (!out_dev || w < 1 || h < 1 || pitch < w) return IDF_EINVAL;

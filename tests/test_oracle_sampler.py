@@ -181,3 +181,27 @@ def test_conditioning_closed_form_two_level():
     cond = Lc[np.ix_(ys, xs)]
     ref = _closed_form_pixelwise(fine_lv, 4, 1, y0, x0, h, w, lambda J, ci, k: ci * J + cond)
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+# ----------------------------------------------------------- eager world (stored-fixture route)
+
+def test_eager_world_with_pool_equals_lazy_world():
+    # EagerWorld (Eq. 1 over the cone of the decode's halo, F evaluated in
+    # worker processes) against the lazy Alg. 1 world: model units and metres
+    from oracle import parallel as P
+    st = synth.small_hier_stack(steps=1, fine_channels=(8, 16), coarse_channels=(8, 8))
+    wts = _weights(st)
+    y0, x0, h, w = 5, -7, 12, 10
+    pool = P.PoolForward(st, wts, 2)
+    try:
+        ew = S.EagerWorld(3, st, wts, y0, x0, h, w, metres=True, fmap=pool.fmap)
+    finally:
+        pool.close()
+    lz = S.World(3, st, wts)
+    m_e, m_l = ew.model(y0, x0, h, w), lz.model(y0, x0, h, w)
+    v_e, v_l = ew.metres(y0, x0, h, w), lz.metres(y0, x0, h, w)
+    assert np.max(np.abs(m_e - m_l)) <= 1e-12 * np.max(np.abs(m_l))
+    assert np.max(np.abs(v_e - v_l)) <= 1e-12 * np.max(np.abs(v_l))
+    # the pooled F equals the serial one up to BLAS summation order
+    e2 = S.EagerWorld(3, st, wts, y0, x0, h, w)
+    assert np.max(np.abs(e2.model(y0, x0, h, w) - m_e)) <= 1e-13 * np.max(np.abs(m_e))
