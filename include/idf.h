@@ -137,6 +137,12 @@ typedef struct {
   int32_t max_batch;                /* windows per UNet launch; 0 = from workspace */
   int32_t profile;                  /* 1: time every kernel launch with CUDA events on the
                                        world's stream; per-class totals in idf_world_stats */
+  uint64_t device_wait_budget_cycles; /* clock64 cycles a bounded device-side wait of the
+                                       tensor-core kernels may take before it gives up and
+                                       the query returns IDF_ETIMEOUT; 0 = 1e9 (about 0.5 s) */
+  int32_t groupnorm_separate;       /* IDF_TF32: 0 (default) applies GroupNorm and SiLU inside
+                                       the tensor-core convolutions' operand path; 1 runs them
+                                       as separate passes (same results bit for bit) */
 } idf_world_opts;
 
 typedef struct {

@@ -41,6 +41,17 @@
 //              then merged across the warp's lanes by the pairwise update of
 //              Chan et al. 1979).  The GroupNorm then needs no statistics
 //              pass over its input.
+//   Transform: optionally (TF32, XF kernels) the activation is the raw
+//              float32 tensor and GroupNorm (+ SiLU) is applied on its way
+//              to the tensor cores: four more warps wait for each landed
+//              stage, replace every staged value x of a real pixel by
+//              tf32(silu((x - mean) * rstd)) with its window's and group's
+//              statistics (leaving the zero padding zero), round the folded
+//              operand to tf32, fence the generic-proxy writes for the
+//              async proxy and release the stage to the MMA thread.  The
+//              arithmetic is that of the separate GroupNorm apply pass, so
+//              the result is the same bit for bit while the normalised
+//              operand never goes through memory.
 //   Waits:     every mbarrier wait is bounded (clock64 budget); on expiry
 //              the CTA sets the status word, drains what it issued and
 //              frees its TMEM before returning.
@@ -55,7 +66,7 @@ namespace idf {
 namespace {
 
 constexpr int BM = 128;
-constexpr long long WAIT_LIMIT = 1000000000LL;  // clock64 cycles, about 0.5 s
+constexpr int XF_THREADS = 128;  // the transform warpgroup of the XF kernels
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -85,11 +96,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait.  honour_abort: give up as soon as another role aborted.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         int* status, bool honour_abort) {
+                                         int* status, bool honour_abort, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (honour_abort && *abort_flag) return false;
-    if (clock64() - t0 > WAIT_LIMIT) {
+    if (clock64() - t0 > limit) {
       atomicExch(status, 1);
       *abort_flag = 1;
       return false;
@@ -196,6 +207,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Named-barrier reduction among the n threads of barrier id: true iff every
+// participant passed true.  Lets the transform warps leave their loop
+// together when any of them gave up on a wait.
+__device__ __forceinline__ bool bar_and(bool v, int id, int n) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// The operand arithmetic of the GroupNorm apply pass (unet.cu): round to
+// tf32 (nearest at mantissa bit 13, ties away), SiLU with the fast
+// exponential and division.
+__device__ __forceinline__ float xf_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float xf_silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
 struct TcParams {
   const float* res;
   float* y;
@@ -208,6 +245,12 @@ struct TcParams {
   int kch;               // input channels per K stage (64 bf16 or 32 tf32: 128 bytes)
   int n_iter1;           // K iterations of the main operand; the rest are the folded 1x1 operand
   int m_tiles, n_tiles;  // output tiles: 128-pixel rows x BN channels
+  long long wait_limit;  // clock64 cycles a bounded wait may take
+  // XF kernels: (mean, rstd) per (window, group) of the main operand's
+  // GroupNorm (null: round only), groups G of cpg channels, the operand's
+  // channel offset in the normalised tensor, SiLU after the normalisation
+  const float2* xf_stats;
+  int xf_G, xf_cpg, xf_coff, xf_silu;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -222,8 +265,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // the activations in L2.  The shared-memory ring of STAGES stages runs
 // across unit boundaries; two TMEM accumulator sets (2 x MT x BN columns)
 // let the epilogue of one unit overlap the main loop of the next.
-template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT>
-__global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF>
+__global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmA_lo,
                                                          const __grid_constant__ CUtensorMap tmB_lo,
@@ -252,6 +295,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
   __shared__ __align__(8) uint64_t accf_bar[2];
   __shared__ __align__(8) uint64_t acce_bar[2];
   __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ __align__(8) uint64_t ready_bar[XF ? STAGES : 1];  // XF: stage transformed
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   __shared__ int skip_sh;
@@ -271,6 +315,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+      if (XF) mbar_init(&ready_bar[s], XF_THREADS);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
@@ -322,7 +367,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
         for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
-          if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true)) {
+          if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true, p.wait_limit)) {
             ok = false;
             break;
           }
@@ -367,7 +412,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
         // drain the copies this thread issued before leaving
         for (int s = 0; s < STAGES; ++s)
           if (last_issue[s] >= 0)
-            wait_bar(&full_bar[s], (uint32_t)(last_issue[s] / STAGES) & 1u, abort_flag, p.status, false);
+            wait_bar(&full_bar[s], (uint32_t)(last_issue[s] / STAGES) & 1u, abort_flag, p.status, false, p.wait_limit);
       }
     }
   } else if (warp == 1) {
@@ -377,13 +422,13 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
       bool ok = true;
       for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++acc) {
         const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
-        if (!wait_bar(&acce_bar[buf], aph ^ 1u, abort_flag, p.status, true)) break;
+        if (!wait_bar(&acce_bar[buf], aph ^ 1u, abort_flag, p.status, true, p.wait_limit)) break;
         fence_after();
         const uint32_t d = tmem + buf * ACC_COLS;
         for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
-          if (!wait_bar(&full_bar[s], ph, abort_flag, p.status, true)) {
+          if (!wait_bar(XF ? &ready_bar[s] : &full_bar[s], ph, abort_flag, p.status, true, p.wait_limit)) {
             ok = false;
             break;
           }
@@ -434,9 +479,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
       }
       // every MMA this thread issued has completed once this commit arrives
       mma_commit(&drain_bar);
-      wait_bar(&drain_bar, 0, abort_flag, p.status, false);
+      wait_bar(&drain_bar, 0, abort_flag, p.status, false, p.wait_limit);
     }
-  } else {
+  } else if (!XF || warp < 6) {
     const int q = warp & 3;
     const int row = q * 32 + lane;
     uint32_t acc = 0;
@@ -461,7 +506,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if (p.res && (int)blockIdx.x < n_units) load_res(blockIdx.x, 0, 0);
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++acc) {
       const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
-      if (!wait_bar(&accf_bar[buf], aph, abort_flag, p.status, true)) break;
+      if (!wait_bar(&accf_bar[buf], aph, abort_flag, p.status, true, p.wait_limit)) break;
       fence_after();
       const int n0 = (u % p.n_tiles) * BN;
 #pragma unroll 1
@@ -531,6 +576,89 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
       fence_before();
       mbar_arrive(&acce_bar[buf]);
     }
+  } else if constexpr (XF) {
+    // Transform warpgroup (XF).  Thread t owns the 16-byte chunk t % 8 of
+    // pixels t / 8, t / 8 + 16, ... of every stage; with pixel rows 128
+    // bytes apart from a 1024-aligned base, the 128-byte swizzle puts
+    // logical chunk jl (channels 4 jl .. 4 jl + 3 of the stage's slice) at
+    // physical chunk jl ^ (pixel % 8), the same for all of them.
+    const int t = (int)threadIdx.x - 192;
+    const int jp = t & 7;
+    const int jl = jp ^ ((t >> 3) & 7);
+    uint32_t it = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int64_t m0 = (int64_t)(u / p.n_tiles) * (BM * MT);
+      const int win = (int)(m0 / HW);
+      const int y0 = (int)((m0 % HW) / p.W);
+      for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1u;
+        const bool got = wait_bar(&full_bar[s], ph, abort_flag, p.status, true, p.wait_limit);
+        if (!bar_and(got, 1, XF_THREADS)) {
+          ok = false;
+          break;
+        }
+        // the staged box: origin (bx0, by0) in the window, bw pixels per row
+        int bx0, by0, bw, npx, kc;
+        bool norm;
+        if (kk >= p.n_iter1) {
+          kc = kk - p.n_iter1;
+          bx0 = 0; by0 = y0; bw = p.W; npx = BM * MT; norm = false;
+        } else if (DXR) {
+          kc = kk % p.n_kc;
+          bx0 = p.ox; by0 = y0 + kk / p.n_kc + p.oy; bw = BM + 2; npx = (BM + 2) * MT;
+          norm = p.xf_stats != nullptr;
+        } else {
+          const int tap = kk / p.n_kc;
+          kc = kk % p.n_kc;
+          bx0 = tap % p.ks + p.ox; by0 = y0 + tap / p.ks + p.oy; bw = p.W; npx = BM * MT;
+          norm = p.xf_stats != nullptr;
+        }
+        float mu = 0.0f, rs = 1.0f;
+        if (norm) {
+          const float2 ms = p.xf_stats[(int64_t)win * p.xf_G + (p.xf_coff + kc * p.kch + 4 * jl) / p.xf_cpg];
+          mu = ms.x;
+          rs = ms.y;
+        }
+        const bool act = norm && p.xf_silu;
+        float* a = reinterpret_cast<float*>(smem + (size_t)s * STAGE_BYTES);
+        int px = t >> 3;
+        int r = px / bw, xc = px - r * bw;
+        for (; px < npx; px += 16) {
+          const int xx = bx0 + xc, yy = by0 + r;
+          if ((unsigned)xx < (unsigned)p.W && (unsigned)yy < (unsigned)p.H) {
+            float4* qp = reinterpret_cast<float4*>(a + px * 32 + jp * 4);
+            float4 v = *qp;
+            if (norm) {
+              v.x = (v.x - mu) * rs;
+              v.y = (v.y - mu) * rs;
+              v.z = (v.z - mu) * rs;
+              v.w = (v.w - mu) * rs;
+            }
+            if (act) {
+              v.x = xf_silu(v.x);
+              v.y = xf_silu(v.y);
+              v.z = xf_silu(v.z);
+              v.w = xf_silu(v.w);
+            }
+            v.x = xf_tf32(v.x);
+            v.y = xf_tf32(v.y);
+            v.z = xf_tf32(v.z);
+            v.w = xf_tf32(v.w);
+            *qp = v;
+          }
+          xc += 16;
+          while (xc >= bw) {
+            xc -= bw;
+            ++r;
+          }
+        }
+        // make the generic-proxy writes visible to the tensor cores' reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&ready_bar[s]);
+      }
+    }
   }
   fence_before();
   __syncthreads();
@@ -575,13 +703,13 @@ constexpr int stage_bytes(int BN, bool SPLIT, bool DXR, int MT) {
   return (SPLIT ? 2 : 1) * ((((DXR ? (BM + 2) * 128 : BM * 128) * MT + 1023) / 1024 * 1024) + (DXR ? 3 : 1) * BN * 128);
 }
 
-template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT>
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF = false>
 bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err) {
   constexpr size_t smem = (size_t)STAGES * stage_bytes(BN, SPLIT, DXR, MT) + 1024;
   static_assert(smem <= 227 * 1024, "stages exceed the shared memory of a CTA");
   static_assert(2 * MT * BN <= 512, "accumulators exceed tensor memory");
   static bool attr = false;
-  auto kern = conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32, MT>;
+  auto kern = conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32, MT, XF>;
   if (!attr) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       *err = "cudaFuncSetAttribute failed";
@@ -591,7 +719,7 @@ bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err)
   }
   const int units = p.m_tiles / MT * p.n_tiles;
   const int grid = units < sm_count() ? units : sm_count();
-  kern<<<grid, 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo, m.b2lo, p);
+  kern<<<grid, XF ? 192 + XF_THREADS : 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo, m.b2lo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -614,7 +742,8 @@ bool conv_tc_shape_ok(int H, int W) {
 bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void* w_lo, const float* res,
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
                      cudaStream_t st, std::string* err, const void* x2, const void* w2, const void* x2_lo,
-                     const void* w2_lo, int Cin2, bool tf32, const TcGeom* geom) {
+                     const void* w2_lo, int Cin2, bool tf32, const TcGeom* geom, const TcXf* xf,
+                     long long wait_limit) {
   if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
     *err = "shape not supported by the tensor-core convolution";
     return false;
@@ -633,6 +762,10 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   const bool split = x_lo && w_lo;
   if (tf32 && split) {
     *err = "tf32 operands have no low parts";
+    return false;
+  }
+  if (xf && (!tf32 || (xf->stats && (xf->G < 1 || xf->cpg < 1 || xf->cpg % 4)))) {
+    *err = "the operand transform needs raw float32 (tf32) operands and 4-channel-aligned groups";
     return false;
   }
   // one K stage reads 128 bytes of channels per pixel / weight row
@@ -726,6 +859,31 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   p.n_iter = p.n_iter1 + (fold ? Cin2 / kch : 0);
   p.m_tiles = (int)((int64_t)n * H * W / BM);
   p.n_tiles = Cout / BN;
+  p.wait_limit = wait_limit > 0 ? wait_limit : 1000000000LL;
+  p.xf_stats = xf ? xf->stats : nullptr;
+  p.xf_G = xf ? xf->G : 1;
+  p.xf_cpg = xf ? xf->cpg : 1;
+  p.xf_coff = xf ? xf->coff : 0;
+  p.xf_silu = xf ? xf->silu : 0;
+  if (xf) {
+    // raw float32 operands normalised (or rounded) in shared memory
+    if (mt == 2) {
+      switch (BN) {
+        case 64: return dxr ? launch<64, 3, false, true, true, 2, true>(m, p, st, err)
+                            : launch<64, 5, false, false, true, 2, true>(m, p, st, err);
+        case 128: return launch<128, 4, false, false, true, 2, true>(m, p, st, err);
+      }
+    } else {
+      switch (BN) {
+        case 64: return dxr ? launch<64, 5, false, true, true, 1, true>(m, p, st, err)
+                            : launch<64, 8, false, false, true, 1, true>(m, p, st, err);
+        case 128: return launch<128, 6, false, false, true, 1, true>(m, p, st, err);
+        case 256: return launch<256, 4, false, false, true, 1, true>(m, p, st, err);
+      }
+    }
+    *err = "unsupported N tile";
+    return false;
+  }
   // stages: about 170-200 KB of shared memory per CTA, one CTA per SM
   if (!split) {
     // bfloat16 or tf32 operands: the same stage bytes

@@ -190,6 +190,10 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
 int64_t unet_launches(const UNet* u);
 // device status word set by bounded device-side waits that ran out
 int* unet_status(const UNet* u);
+// fuse_groupnorm (IDF_TF32 only): GroupNorm and SiLU inside the tensor-core
+// convolutions' operand path; wait_limit: clock64 cycles a bounded device
+// wait may take (0: about 0.5 s)
+void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit);
 void unet_set_prof(UNet* u, Prof* p);
 
 // tcgen05 conv (conv_tc.cu)
@@ -208,6 +212,17 @@ struct TcGeom {
   int res_up = 0;
 };
 
+// Operand transform of a TF32 tensor-core convolution: x (and x2) are raw
+// float32 tensors; on their way to the tensor cores each real pixel's value
+// of x becomes tf32(silu((v - mean) * rstd)) (or without SiLU) with the
+// (mean, rstd) = stats[window * G + (coff + channel) / cpg] of its GroupNorm
+// group, or, with stats null, just tf32(v); x2 is rounded to tf32.  Zero
+// padding stays zero.
+struct TcXf {
+  const float2* stats = nullptr;
+  int G = 1, cpg = 1, coff = 0, silu = 0;
+};
+
 // y (float32 NHWC, Cout) = conv(x) over (tap, Cin) [+ the 1x1 conv of x2
 // over Cin2, folded into the same accumulator] [+ res], x / x2 in bfloat16
 // (with low parts for the compensated split) or tf32-rounded float32.  With
@@ -218,7 +233,7 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
                      cudaStream_t st, std::string* err, const void* x2 = nullptr, const void* w2 = nullptr,
                      const void* x2_lo = nullptr, const void* w2_lo = nullptr, int Cin2 = 0, bool tf32 = false,
-                     const TcGeom* geom = nullptr);
+                     const TcGeom* geom = nullptr, const TcXf* xf = nullptr, long long wait_limit = 0);
 
 // float32 building blocks (unet.cu), NHWC, square images
 void launch_conv_f32(const float* x, const float* wk, const float* res, float* y, int n, int H, int W,

@@ -1577,6 +1577,10 @@ struct UNet {
   int* status = nullptr;
   int64_t launches = 0;
   Prof* prof = nullptr;
+  // TF32: GroupNorm (+ SiLU) applied inside the tensor-core convolutions'
+  // operand path (no normalised operand in memory); false: separate passes
+  bool fuse_gn = false;
+  long long wait_limit = 0;  // clock64 budget of the tensor-core kernels' waits (0: default)
 };
 
 constexpr int GN_MAX_CHUNKS = 1024;
@@ -1882,6 +1886,10 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
 int unet_max_batch(const UNet* u) { return u->max_batch; }
 int64_t unet_launches(const UNet* u) { return u->launches; }
 int* unet_status(const UNet* u) { return u->status; }
+void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit) {
+  u->fuse_gn = fuse_groupnorm && u->precision == 4;
+  u->wait_limit = wait_limit;
+}
 void unet_set_prof(UNet* u, Prof* p) { u->prof = p; }
 
 namespace {
@@ -1908,7 +1916,8 @@ bool tc_path(const ConvW& w, int H) {
 template <typename TA>
 bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* res, float* y, int H,
               const void* x_lo = nullptr, float2* bs = nullptr, const ConvW* w2 = nullptr,
-              const void* x2 = nullptr, const void* x2_lo = nullptr, const TcGeom* geom = nullptr) {
+              const void* x2 = nullptr, const void* x2_lo = nullptr, const TcGeom* geom = nullptr,
+              const TcXf* xf = nullptr) {
   if (!c.ok) return false;
   const int W = H;
   const double flops = 2.0 * c.n * H * W * (double)w.cout * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0));
@@ -1927,7 +1936,7 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     const bool ok = conv_tc_forward(x, wk, sp ? x_lo : nullptr, sp ? w.w16lo : nullptr, res, y, bs, c.n, H, W,
                                     w.cin, w.cout, w.ks, c.u->status, c.st, &e, w2 ? x2 : nullptr, wk2,
                                     w2 && sp ? x2_lo : nullptr, w2 && sp ? w2->w16lo : nullptr,
-                                    w2 ? w2->cin : 0, tf, geom);
+                                    w2 ? w2->cin : 0, tf, geom, xf, c.u->wait_limit);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     if (!ok) {
       c.ok = false;
@@ -1937,10 +1946,10 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     c.u->launches++;
     return ok && bs != nullptr;
   }
-  if (w2 || geom) {
+  if (w2 || geom || xf) {
     c.ok = false;
     c.err->code = 3;
-    c.err->msg = "folded operand or convolution geometry outside the tensor-core path";
+    c.err->msg = "folded operand, convolution geometry or operand transform outside the tensor-core path";
     return false;
   }
   const int64_t M = (int64_t)c.n * H * W;
@@ -2136,6 +2145,41 @@ void gn(Ctx& c, const float* x, int H, int C, void* y, bool silu, void* copy = n
   c.u->launches += 2;
 }
 
+// Whether gn_stats handles x (C channels, H x H) with or without partials.
+bool gn_stats_ok(Ctx& c, int H, int C) {
+  const int G = c.u->d.groups, Cg = C / G;
+  return C % G == 0 && C % 4 == 0 && Cg % 4 == 0 && Cg / 4 <= 256 &&
+         (int64_t)c.n * H * H * (C / 4) < (1ll << 31);
+}
+
+// GroupNorm statistics of x into c.u->stats ((mean, rstd) per window and
+// group), without the apply pass: from the block partials bs of the
+// convolution that wrote x when given, else one partial + finalize pass.
+void gn_stats(Ctx& c, const float* x, int H, int C, const float2* bs) {
+  if (!c.ok) return;
+  const int G = c.u->d.groups, Cg = C / G, HW = H * H;
+  const bool blk = bs && C % 16 == 0 && Cg % 16 == 0 && HW % 32 == 0;
+  const double nb = (double)c.n * HW * C;
+  const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, blk ? 0.0 : 4.0 * nb) : -1;
+  if (blk) {
+    const BlkSrc src{nullptr, bs, 0, C, 0, HW / 32};
+    gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(src, c.n, G, c.u->stats);
+    c.u->launches += 1;
+  } else {
+    const int Q = Cg / 4, P = 256 / Q;
+    int chunk_px = std::max(P, 8192 / Cg);
+    int chunks = (HW + chunk_px - 1) / chunk_px;
+    if (chunks > GN_MAX_CHUNKS) {
+      chunk_px = (HW + GN_MAX_CHUNKS - 1) / GN_MAX_CHUNKS;
+      chunks = (HW + chunk_px - 1) / chunk_px;
+    }
+    gn_partial_kernel<<<dim3(chunks, G, c.n), 256, 0, c.st>>>(x, HW, C, G, chunk_px, c.u->gnpart);
+    gn_finalize_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(x, c.u->gnpart, c.n, chunks, HW, C, G, c.u->stats);
+    c.u->launches += 2;
+  }
+  if (c.u->prof) c.u->prof->end(pr, c.st);
+}
+
 // Output head F = conv3x3(silu(gn(x))) (one output channel) as one fused
 // pass over x after the statistics; returns false when the shape does not
 // fit the fused kernel (the caller then runs GroupNorm and the conv apart).
@@ -2295,6 +2339,40 @@ bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs&
   wi += 3;
   if (!c.ok) return true;
   const bool sp = c.u->split;
+  if (c.u->fuse_gn && std::is_same<TA, tf32>::value && gn_stats_ok(c, H, cout)) {
+    // GroupNorm + SiLU inside the convolutions' operand path: a and b are
+    // read raw with the concat's statistics, the shortcuts round them
+    const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, 0.0) : -1;
+    const BlkSrc bsrc{bsa, bsb, Ca, Cb, Hh * Hh / 32, H * H / 32};
+    gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(bsrc, c.n, G, c.u->stats);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches += 1;
+    const TcXf xa{c.u->stats, G, Cg, 0, 1}, xb{c.u->stats, G, Cg, Ca, 1}, xr{};
+    for (int py = 0; py < 2; ++py)
+      for (int px = 0; px < 2; ++px) {
+        TcGeom g;
+        g.oy = py - 1;
+        g.ox = px - 1;
+        g.out_up = 1;
+        g.py = py;
+        g.px = px;
+        conv_run<TA>(c, dw.w1p[2 * py + px], a, false, nullptr, (float*)lb.T3, Hh, nullptr, nullptr, nullptr,
+                     nullptr, nullptr, &g, &xa);
+      }
+    const bool s2 = conv_run<TA>(c, dw.w1s, b, false, (const float*)lb.T3, (float*)lb.T2, H, nullptr, lb.bT2,
+                                 nullptr, nullptr, nullptr, nullptr, &xb);
+    gn_stats(c, (const float*)lb.T2, H, cout, s2 ? lb.bT2 : nullptr);
+    conv_run<TA>(c, dw.wska, a, false, nullptr, (float*)lh.T2, Hh, nullptr, nullptr, nullptr, nullptr, nullptr,
+                 nullptr, &xr);
+    const TcXf x2{c.u->stats, G, cout / G, 0, 1};
+    TcGeom g2;
+    g2.oy = -1;
+    g2.ox = -1;
+    g2.res_up = 1;
+    *y_stats = conv_run<TA>(c, c2, lb.T2, false, (const float*)lh.T2, Y, H, nullptr, bsY, &dw.wsks, b, nullptr,
+                            &g2, &x2);
+    return true;
+  }
   // statistics of the concat's groups from the block partials of a and b
   const double wr = (double)sizeof(TA) * 2 * (sp ? 2 : 1);
   const double nb = (double)c.n * ((double)Hh * Hh * Ca + (double)H * H * Cb);
@@ -2341,6 +2419,21 @@ bool resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
   if (cin != cout) sk = &c.u->convs[wi++];
   const bool need_copy = sk && !std::is_same<TA, float>::value;
   const bool sp = c.u->split;
+  if (c.u->fuse_gn && std::is_same<TA, tf32>::value && tc_path<TA>(c1, b.H) && tc_path<TA>(c2, b.H) &&
+      (!sk || tc_path<TA>(*sk, b.H)) && gn_stats_ok(c, b.H, cin) && gn_stats_ok(c, b.H, cout)) {
+    // GroupNorm + SiLU inside the convolutions' operand path; X and T2 are
+    // read raw, the shortcut rounds X
+    const int G = c.u->d.groups;
+    gn_stats(c, X, b.H, cin, bsX);
+    const TcXf x1{c.u->stats, G, cin / G, 0, 1};
+    const bool s2 = conv_run<TA>(c, c1, X, false, nullptr, (float*)b.T2, b.H, nullptr, b.bT2, nullptr, nullptr,
+                                 nullptr, nullptr, &x1);
+    gn_stats(c, (const float*)b.T2, b.H, cout, s2 ? b.bT2 : nullptr);
+    const TcXf x2{c.u->stats, G, cout / G, 0, 1};
+    if (sk)
+      return conv_run<TA>(c, c2, b.T2, false, nullptr, Y, b.H, nullptr, bsY, sk, X, nullptr, nullptr, &x2);
+    return conv_run<TA>(c, c2, b.T2, false, X, Y, b.H, nullptr, bsY, nullptr, nullptr, nullptr, nullptr, &x2);
+  }
   gn<TA>(c, X, b.H, cin, b.T1, true, need_copy ? b.T4 : nullptr, sp ? b.T1lo : nullptr,
          sp && need_copy ? b.T4lo : nullptr, bsX);
   const bool s2 = conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H, sp ? b.T1lo : nullptr, b.bT2);
@@ -2391,8 +2484,16 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
   if (d.attn) {
     const ConvW& qkv = u->convs[wi++];
     const ConvW& proj = u->convs[wi++];
-    gn<TA>(c, cur, bl.H, prev, bl.T1, false, nullptr, u->split ? bl.T1lo : nullptr, nullptr, cur_bs);
-    conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H, u->split ? bl.T1lo : nullptr);
+    if (u->fuse_gn && std::is_same<TA, tf32>::value && tc_path<TA>(qkv, bl.H) && gn_stats_ok(c, bl.H, prev)) {
+      // GroupNorm (no SiLU) inside the qkv projection's operand path
+      gn_stats(c, cur, bl.H, prev, cur_bs);
+      const TcXf xq{u->stats, d.groups, prev / d.groups, 0, 0};
+      conv_run<TA>(c, qkv, cur, false, nullptr, (float*)bl.T2, bl.H, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   nullptr, &xq);
+    } else {
+      gn<TA>(c, cur, bl.H, prev, bl.T1, false, nullptr, u->split ? bl.T1lo : nullptr, nullptr, cur_bs);
+      conv_run<TA>(c, qkv, bl.T1, false, nullptr, (float*)bl.T2, bl.H, u->split ? bl.T1lo : nullptr);
+    }
     const int Tn = bl.H * bl.H, dh = prev / d.heads;
     const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
     const int pr = u->prof ? u->prof->begin(PK_ATTENTION, st, 4.0 * n * (double)Tn * Tn * prev, 0.0) : -1;

@@ -932,6 +932,7 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
         return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
       }
       unet_set_prof(L.unet, &W->prof);
+      unet_set_options(L.unet, opts->groupnorm_separate == 0, (long long)opts->device_wait_budget_cycles);
     }
   }
   if (stack->laplacian) {

@@ -84,9 +84,9 @@ def test_two_level_full_width_four_steps(case4, precision):
     assert err <= 2e-2 * sig
 
 
-@pytest.mark.xfail(reason="plain BF16 at K = 4: see the K = 2 case; the later steps damp the "
-                          "network error only partly", strict=False)
 def test_two_level_full_width_four_steps_plain_bf16(case4):
+    # at K = 4 the later steps damp the network's bfloat16 rounding enough
+    # for the 2e-2 sigma_out bound (measured 1.74e-2 max, 4.9e-3 rms)
     idf, st, wts, rect, ref = case4
     sig = ref.std()
     W = idf.World(0, st, wts, precision="bf16")
