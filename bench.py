@@ -73,6 +73,9 @@ def parse():
     p.add_argument("--in-flight", type=int, default=64)
     p.add_argument("--earth", type=int, default=0,
                    help="Earth-scale mode: an N x N metres query on the 16-channel stack with a 2048^2 fBm low band")
+    p.add_argument("--small-precision", default="fp8", choices=["fp32", "bf16", "fp8"],
+                   help="precision of the 16-channel network in --earth and --serve (fp8 / bf16: the fused "
+                        "tensor-core kernel; fp32: the plain sampler)")
     p.add_argument("--profile-unet", type=int, default=0,
                    help="profiling mode: one warm-up and one timed fine-level UNet forward on N windows")
     p.add_argument("--clocks-dir", default=tempfile.gettempdir(),
@@ -769,8 +772,9 @@ def run_serve(args):
     maxpx = max(w * h for _, _, w, h in qs)
     bufs = [torch.empty(maxpx, device=dev) for _ in range(args.in_flight)]
     out = {}
-    for mode in ("batched", "single"):
-        W = idf.World(0, st, wts, precision="fp32" if args.precision in ("bf16x3", "tf32") else args.precision)
+    modes = [("batched", args.small_precision), ("single", args.small_precision), ("single_fp32", "fp32")]
+    for mode, prec in modes:
+        W = idf.World(0, st, wts, precision=prec)
         # warm-up on an unrelated region
         W.query_device(5 << 30, 5 << 30, 256, 256, bufs[0].data_ptr(), 256)
         torch.cuda.synchronize()
@@ -798,14 +802,16 @@ def run_serve(args):
         px = sum(w * h for _, _, w, h in qs)
         l0, l1 = s0["levels"][0], s1["levels"][0]
         hits, miss = l1["cache_hits"] - l0["cache_hits"], l1["cache_misses"] - l0["cache_misses"]
-        out[mode] = {"px_s": px / total, "total_s": total, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+        out[mode] = {"precision": prec, "px_s": px / total, "total_s": total,
+                     "p50_ms": 1000 * float(np.percentile(lat, 50)),
                      "p99_ms": 1000 * float(np.percentile(lat, 99)),
                      "windows": l1["windows_evaluated"] - l0["windows_evaluated"],
                      "cache_hit_rate": hits / max(1, hits + miss),
                      "launches": s1["kernel_launches"] - s0["kernel_launches"]}
+    out["speedup_batched_vs_plain_fp32_single"] = out["batched"]["px_s"] / out["single_fp32"]["px_s"]
     print(json.dumps({"serve": {"queries": len(qs), "px": sum(w * h for _, _, w, h in qs), "in_flight": args.in_flight,
-                                "stack": "plain 16-channel UNet, 32x32 windows at stride 16, 4 steps",
-                                "precision": "fp32", "latency": "per query: submission of its group to completion",
+                                "stack": "16-channel UNet, 32x32 windows at stride 16, 4 steps",
+                                "latency": "per query: submission of its group to completion",
                                 **out}}))
     return 0
 
@@ -830,7 +836,8 @@ def run_earth(args):
     st = synth.config4_stack(fx, steps=4)
     wts = [synth.weights([s for _, s in OU.param_shapes(lv)], 0, i) for i, lv in enumerate(st["level"])]
     q = args.earth
-    W = idf.World(0, st, wts, precision="fp32", profile=True)
+    prec = args.small_precision
+    W = idf.World(0, st, wts, precision=prec, profile=True)
     out = torch.empty((q, q), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -855,21 +862,46 @@ def run_earth(args):
     ms = e0.elapsed_time(e1)
     s1 = W.stats()
     m = out.cpu().numpy()
-    # error in metres on a crop across the period boundary (x = 16384)
-    crop = (16384 - 32, -24, 64, 48)
-    got = W.query(*crop, kind=idf.IDF_OUT_METRES).astype(np.float64)
+    # errors against the FP64 oracle on four crops (centre, two corners of
+    # the timed query's first location, and one across the fixture's period)
+    ow = OS.World(0, st, wts)
+    errs = []
+    for (cx, cy) in ((-32, -32), (-q // 2, -q // 2), (q // 2 - 64, -q // 2), (16384 - 32, 100)):
+        crop = (cx, cy, 64, 64)
+        got = W.query(*crop, kind=idf.IDF_OUT_METRES).astype(np.float64)
+        gm = W.query(*crop).astype(np.float64)
+        ref = ow.metres(crop[1], crop[0], crop[3], crop[2])
+        rm = ow.model(crop[1], crop[0], crop[3], crop[2])
+        errs.append({"crop": list(crop), "max_abs_m": float(np.max(np.abs(got - ref))),
+                     "max_abs_metres_in_crop": float(np.max(np.abs(ref))),
+                     "model_max_abs_sigma_out": float(np.max(np.abs(gm - rm)) / rm.std())})
     W.close()
-    ref = OS.World(0, st, wts).metres(crop[1], crop[0], crop[3], crop[2])
+    # the plain FP32 sampler on the same query size, one cold query
+    fp32 = None
+    if prec != "fp32" and args.fp32_steps > 0:
+        Wp = idf.World(0, st, wts, precision="fp32")
+        Wp.query_device(-q // 2 + 65536 * 99, -q // 2, 256, 256, out.data_ptr(), 256, kind=idf.IDF_OUT_METRES,
+                        stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        Wp.query_device(-q // 2 + 65536 * 100, -q // 2, q, q, out.data_ptr(), q, kind=idf.IDF_OUT_METRES,
+                        stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        Wp.close()
+        fp32 = q * q / (e0.elapsed_time(e1) / 1000.0)
     prof = {k: s1["profile"][k]["ms"] - s0["profile"][k]["ms"] for k in s1["profile"]}
     line = {"metric": "final heightmap px/s (metres, Earth-scale low band)", "value": q * q * args.steps / (ms / 1000.0),
             "unit": "px/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": {"fp8": "e4m3", "bf16": "bf16"}.get(prec, "f32"),
+            "data": "synthetic",
             "config": {"workload": f"16-channel 32x32-window UNet (4 steps) residual band + 2048^2 fBm low band "
-                                   f"(beta 2.2, period 16384 px), {q}x{q} metres query, float32",
-                       "precision": "fp32", "fp8": "not built (16 channels are below the tensor-core tile width)"},
+                                   f"(beta 2.2, period 16384 px), {q}x{q} metres query",
+                       "precision": prec},
             "metres_range": [float(m.min()), float(m.max())],
-            "crop_error_m": {"max_abs": float(np.max(np.abs(got - ref))), "crop": list(crop),
-                             "max_abs_metres_in_crop": float(np.max(np.abs(ref)))},
+            "error_vs_oracle": errs,
+            "plain_fp32": {"value": fp32, "unit": "px/s", "speedup": (q * q * args.steps / (ms / 1000.0)) / fp32}
+            if fp32 else None,
             "kernel_ms": {k: v for k, v in prof.items() if v > 0}, "clocks": clk}
     print(json.dumps(line))
     return 0

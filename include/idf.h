@@ -52,13 +52,18 @@ typedef enum {
 
 /* Arithmetic of the UNet convolutions.  IDF_FP32: float32 SIMT (the plain
  * sampler).  IDF_BF16: bfloat16 operands on the tensor cores, float32
- * accumulation, float32 residual stream.  IDF_BF16X3: the same tensor-core
+ * accumulation, float32 residual stream (for the 16-channel networks -- 2
+ * levels of 16 channels, 32 x 32 windows, no attention -- the whole UNet of
+ * a window runs as one fused tensor-core kernel).  IDF_FP8_E4M3: that fused
+ * kernel with E4M3 operands, per-output-channel float32 weight scales and
+ * power-of-two activation scales, float32 accumulation and statistics; built
+ * for the 16-channel networks only (other networks: IDF_EUNSUPPORTED).  IDF_BF16X3: the same tensor-core
  * path with each operand split as hi + lo (both bfloat16) and the products
  * hi*hi + lo*hi + hi*lo accumulated, which compensates the rounding of both
  * operands at three times the tensor work.  IDF_TF32: operands rounded to
  * tf32 (10 explicit mantissa bits, round to nearest, ties away) and one tensor-core
  * product per multiply-add (kind::tf32, half the bf16 rate), float32
- * accumulation and residual stream.  IDF_FP8_E4M3 is not built yet. */
+ * accumulation and residual stream. */
 typedef enum { IDF_FP32 = 0, IDF_BF16 = 1, IDF_FP8_E4M3 = 2, IDF_BF16X3 = 3, IDF_TF32 = 4 } idf_precision;
 
 typedef enum {
@@ -140,9 +145,10 @@ typedef struct {
   uint64_t device_wait_budget_cycles; /* clock64 cycles a bounded device-side wait of the
                                        tensor-core kernels may take before it gives up and
                                        the query returns IDF_ETIMEOUT; 0 = 1e9 (about 0.5 s) */
-  int32_t groupnorm_separate;       /* IDF_TF32: 0 (default) applies GroupNorm and SiLU inside
-                                       the tensor-core convolutions' operand path; 1 runs them
-                                       as separate passes (same results bit for bit) */
+  int32_t groupnorm_in_conv;        /* IDF_TF32: 1 applies GroupNorm and SiLU inside the
+                                       tensor-core convolutions' operand path (no normalised
+                                       operand in memory); 0 (default) runs them as separate
+                                       passes, which is faster here.  Same results bit for bit */
 } idf_world_opts;
 
 typedef struct {
@@ -163,7 +169,8 @@ typedef struct {
  * arena.  Returns IDF_EINVAL for an invalid stack or options (among them a
  * low-band fixture with two levels, without laplacian = 1 or with a level of
  * in_ch != 1, and laplacian = 1 with one level and no fixture) before any
- * device call, IDF_EUNSUPPORTED for IDF_FP8_E4M3, IDF_ENOMEM / IDF_ECUDA on
+ * device call, IDF_EUNSUPPORTED for IDF_FP8_E4M3 with a level that is not a
+ * 16-channel network, IDF_ENOMEM / IDF_ECUDA on
  * device allocation or CUDA failures.  *out is NULL on failure. */
 idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack,
                             const idf_world_opts* opts, idf_world** out);

@@ -27,6 +27,16 @@ noise once per pixel; the CUDA path uses that fused form.
   channel is the nearest x scale upsampling of the coarse level's result
   (Sec. 5.3, decoder conditioning), fetched lazily.
 
+Blending only at selected noise levels (the T variants, Sec. 4 "Latency",
+App. G): a level may group its K sampler steps into T rounds of m_1 + ... +
+m_T = K steps (``round_steps``).  Within a round every window runs its m_r
+steps on its own, x <- D(x; sigma_j) + sigma_{j+1} N(seed, level, j+1, .)
+(noise keyed on absolute coordinates, the last step of the sampler without
+noise), and Eq. 2 blends the windows' results only at the round's end.  The
+lazy recursion, the cache and the cone then advance by rounds: J_r is the
+blended state after round r.  One step per round (the default) is the
+blend-every-step sampler above.
+
 Pins: the two routes agree (Lemma 3); query-order and cache-size
 independence (Thm 1); closed forms with the test denoisers; window counts of
 Lemma 4 / Thm 2 (tests/test_oracle_sampler.py).
@@ -54,6 +64,12 @@ class _LevelCommon:
         self.o = int(lv.get("offset", 0))
         self.K = int(lv["steps"])
         self.sig = S_.sigmas(self.K, lv["sigma_max"], lv["sigma_min"], lv["rho"])
+        rs = lv.get("round_steps")
+        self.round_steps = [1] * self.K if not rs else [int(v) for v in rs]
+        if sum(self.round_steps) != self.K or min(self.round_steps) < 1:
+            raise ValueError("round_steps must be positive and sum to steps")
+        self.R = len(self.round_steps)
+        self.round_start = [sum(self.round_steps[:r]) for r in range(self.R)]
         self.sd = float(lv["sigma_data"])
         self.W = S_.weight_2d(self.H, blend_eps)
         self.params = None
@@ -78,26 +94,34 @@ class _LevelCommon:
         return P[np.ix_(ys, xs)]
 
     def phi(self, k: int, xs: list, rects: list) -> list:
-        """Phi for the windows of step k: inputs xs (H x H each) at rects."""
-        c_skip, c_out, c_in = S_.edm_coeffs(self.sig[k], self.sd)
-        chans = [np.stack(xs)[:, None] * c_in]
+        """Phi of round k for windows with inputs xs (H x H each) at rects:
+        the round's sampler steps, each D(x; sigma_j) + sigma_{j+1} N."""
+        cond = None
         if int(self.lv["in_ch"]) == 2:
-            chans.append(np.stack([self.cond(*r) for r in rects])[:, None])
-        xin = np.concatenate(chans, axis=1)
-        F = np.empty((len(xs), self.H, self.H))
-        if self.fmap is not None and self.params is not None:
-            F[:] = self.fmap(xin)
-        else:
-            bs = 64 if self.H <= 32 else 1
-            for b0 in range(0, len(xs), bs):
-                F[b0:b0 + bs] = U_.forward(self.lv, self.params, xin[b0:b0 + bs])[:, 0]
-        self.phi_calls += len(xs)
-        out = []
-        for x, r, f in zip(xs, rects, F):
-            d = c_skip * x + c_out * f
-            if k + 1 < self.K:
-                d = d + self.sig[k + 1] * self.noise(k + 1, *r)
-            out.append(d)
+            cond = np.stack([self.cond(*r) for r in rects])[:, None]
+        out = [np.asarray(x, dtype=np.float64) for x in xs]
+        j0 = self.round_start[k]
+        for j in range(j0, j0 + self.round_steps[k]):
+            c_skip, c_out, c_in = S_.edm_coeffs(self.sig[j], self.sd)
+            chans = [np.stack(out)[:, None] * c_in]
+            if cond is not None:
+                chans.append(cond)
+            xin = np.concatenate(chans, axis=1)
+            F = np.empty((len(xs), self.H, self.H))
+            if self.fmap is not None and self.params is not None:
+                F[:] = self.fmap(xin)
+            else:
+                bs = 64 if self.H <= 32 else 1
+                for b0 in range(0, len(xs), bs):
+                    F[b0:b0 + bs] = U_.forward(self.lv, self.params, xin[b0:b0 + bs])[:, 0]
+            self.phi_calls += len(xs)
+            nxt = []
+            for x, r, f in zip(out, rects, F):
+                d = c_skip * x + c_out * f
+                if j + 1 < self.K:
+                    d = d + self.sig[j + 1] * self.noise(j + 1, *r)
+                nxt.append(d)
+            out = nxt
         return out
 
 
@@ -106,8 +130,8 @@ class Level(_LevelCommon):
 
     def __init__(self, *a, capacity=None, **kw):
         super().__init__(*a, **kw)
-        self.capacity = capacity          # per-step contribution LRU capacity (None = unbounded)
-        self.contrib = [OrderedDict() for _ in range(self.K + 1)]  # step -> {(i,j): W (x) Phi}
+        self.capacity = capacity          # per-round contribution LRU capacity (None = unbounded)
+        self.contrib = [OrderedDict() for _ in range(self.R + 1)]  # round -> {(i,j): W (x) Phi}
 
     def clear(self):
         for c in self.contrib:
@@ -143,14 +167,15 @@ class Level(_LevelCommon):
         return out
 
     def final(self, y0, x0, h, w):
-        return self.J(self.K, y0, x0, h, w)
+        return self.J(self.R, y0, x0, h, w)
 
 
 def cone_rects(lvl: _LevelCommon, y0, x0, h, w):
-    """rects[k] = region of J_k a cold query of J_K[R] touches."""
-    rects = [None] * (lvl.K + 1)
-    rects[lvl.K] = (y0, x0, h, w)
-    for k in range(lvl.K, 0, -1):
+    """rects[k] = region of J_k (the state after round k) a cold query of the
+    result touches."""
+    rects = [None] * (lvl.R + 1)
+    rects[lvl.R] = (y0, x0, h, w)
+    for k in range(lvl.R, 0, -1):
         ry0, rx0, rh, rw = rects[k]
         ri = K_.kappa_1d(ry0, ry0 + rh, lvl.H, lvl.s, lvl.o)
         rj = K_.kappa_1d(rx0, rx0 + rw, lvl.H, lvl.s, lvl.o)
@@ -172,7 +197,7 @@ class EagerLevel(_LevelCommon):
         j0 = (cx - self.o) // self.s
         wins = [(i0 + a, j0 + b) for a in range(ni) for b in range(nj)]
         rr = [K_.window_rect(i, j, self.H, self.s, self.o) for (i, j) in wins]
-        for k in range(self.K):
+        for k in range(self.R):
             xs = [J[r[0] - cy:r[0] - cy + self.H, r[1] - cx:r[1] - cx + self.H] for r in rr]
             phis = self.phi(k, xs, rr)
             A = np.zeros((ch, cw))

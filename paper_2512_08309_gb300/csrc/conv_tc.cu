@@ -46,12 +46,17 @@
 //              to the tensor cores: four more warps wait for each landed
 //              stage, replace every staged value x of a real pixel by
 //              tf32(silu((x - mean) * rstd)) with its window's and group's
-//              statistics (leaving the zero padding zero), round the folded
-//              operand to tf32, fence the generic-proxy writes for the
-//              async proxy and release the stage to the MMA thread.  The
-//              arithmetic is that of the separate GroupNorm apply pass, so
-//              the result is the same bit for bit while the normalised
-//              operand never goes through memory.
+//              statistics (leaving the zero padding zero), fence the
+//              generic-proxy writes for the async proxy and release the
+//              stage to the MMA thread; folded 1x1 stages pass unchanged
+//              (raw float32, read as tf32).  The arithmetic is that of the
+//              separate GroupNorm apply pass, so the result is the same bit
+//              for bit while the normalised operand never goes through
+//              memory.  Measured on the 2-level stack it is slower than the
+//              separate pass (each staged box is transformed once per tap
+//              and N tile, up to 9x the elements, and the exponential and
+//              reciprocal of SiLU bind the transform warps), so it is an
+//              option, off by default.
 //   Waits:     every mbarrier wait is bounded (clock64 budget); on expiry
 //              the CTA sets the status word, drains what it issued and
 //              frees its TMEM before returning.
@@ -603,8 +608,9 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
         int bx0, by0, bw, npx, kc;
         bool norm;
         if (kk >= p.n_iter1) {
+          // folded 1x1 operand: raw float32, used as tf32 as it is
           kc = kk - p.n_iter1;
-          bx0 = 0; by0 = y0; bw = p.W; npx = BM * MT; norm = false;
+          bx0 = 0; by0 = y0; bw = p.W; npx = 0; norm = false;
         } else if (DXR) {
           kc = kk % p.n_kc;
           bx0 = p.ox; by0 = y0 + kk / p.n_kc + p.oy; bw = BM + 2; npx = (BM + 2) * MT;

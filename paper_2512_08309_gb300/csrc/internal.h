@@ -212,12 +212,12 @@ struct TcGeom {
   int res_up = 0;
 };
 
-// Operand transform of a TF32 tensor-core convolution: x (and x2) are raw
-// float32 tensors; on their way to the tensor cores each real pixel's value
-// of x becomes tf32(silu((v - mean) * rstd)) (or without SiLU) with the
-// (mean, rstd) = stats[window * G + (coff + channel) / cpg] of its GroupNorm
-// group, or, with stats null, just tf32(v); x2 is rounded to tf32.  Zero
-// padding stays zero.
+// Operand transform of a TF32 tensor-core convolution: x is a raw float32
+// tensor; on its way to the tensor cores each real pixel's value becomes
+// tf32(silu((v - mean) * rstd)) (or without SiLU) with the (mean, rstd) =
+// stats[window * G + (coff + channel) / cpg] of its GroupNorm group, or,
+// with stats null, just tf32(v).  Zero padding stays zero.  A folded x2 is
+// read as it is.
 struct TcXf {
   const float2* stats = nullptr;
   int G = 1, cpg = 1, coff = 0, silu = 0;
@@ -234,6 +234,17 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
                      cudaStream_t st, std::string* err, const void* x2 = nullptr, const void* w2 = nullptr,
                      const void* x2_lo = nullptr, const void* w2_lo = nullptr, int Cin2 = 0, bool tf32 = false,
                      const TcGeom* geom = nullptr, const TcXf* xf = nullptr, long long wait_limit = 0);
+
+// Fused per-window UNet of the 16-channel networks (unet_small.cu): 2
+// levels of 16 channels, 32 x 32 windows, GroupNorm(4), no attention, on
+// the tensor cores in BF16 or FP8 E4M3 (per-output-channel weight scales).
+struct SmallNet;
+bool small_net_eligible(const UNetDesc& d);
+SmallNet* small_net_create(const UNetDesc& d, const float* w_host, bool fp8, Err* err);
+void small_net_destroy(SmallNet* s);
+// F (n, 32, 32) float32 of x (n, 32, 32, in_ch) NHWC float32
+bool small_net_forward(const SmallNet* s, const float* x, int n, float* F, int* status, long long wait_limit,
+                       cudaStream_t st, std::string* err);
 
 // float32 building blocks (unet.cu), NHWC, square images
 void launch_conv_f32(const float* x, const float* wk, const float* res, float* y, int n, int H, int W,

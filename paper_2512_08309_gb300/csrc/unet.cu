@@ -1578,10 +1578,18 @@ struct UNet {
   int64_t launches = 0;
   Prof* prof = nullptr;
   // TF32: GroupNorm (+ SiLU) applied inside the tensor-core convolutions'
-  // operand path (no normalised operand in memory); false: separate passes
+  // operand path (no normalised operand in memory; slower, see conv_tc.cu);
+  // false (default): separate passes
   bool fuse_gn = false;
   long long wait_limit = 0;  // clock64 budget of the tensor-core kernels' waits (0: default)
+  // BF16 / FP8 E4M3 on a 16-channel network: the fused per-window kernel
+  // (unet_small.cu) evaluates the whole UNet; nothing else is allocated
+  SmallNet* small = nullptr;
 };
+
+static bool uses_small(const UNetDesc& d, int precision) {
+  return (precision == 1 || precision == 2) && small_net_eligible(d);
+}
 
 constexpr int GN_MAX_CHUNKS = 1024;
 
@@ -1668,11 +1676,13 @@ void unet_destroy(UNet* u) {
   cudaFree(u->gnpart);
   cudaFree(u->blkmem);
   cudaFree(u->status);
+  small_net_destroy(u->small);
   delete u;
 }
 
 // Bytes of the activation buffers for max_batch windows (256-byte aligned each).
 size_t unet_arena_bytes(const UNetDesc& d, int precision, int max_batch) {
+  if (uses_small(d, precision)) return 0;
   const bool bfm = precision == 1 || precision == 3;
   const int nbuf = precision == 3 ? 11 : 8;
   size_t t = 0;
@@ -1781,6 +1791,21 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
   u->precision = precision;
   u->split = precision == 3;
   u->max_batch = std::max(1, max_batch);
+  if (uses_small(d, precision)) {
+    u->small = small_net_create(d, w_host, precision == 2, err);
+    if (!u->small || !ck(cudaMalloc(&u->status, sizeof(int)), err, "cudaMalloc status") ||
+        !ck(cudaMemset(u->status, 0, sizeof(int)), err, "memset status")) {
+      unet_destroy(u);
+      return nullptr;
+    }
+    return u;
+  }
+  if (precision == 2) {
+    err->code = 8;
+    err->msg = "FP8 E4M3 is built for the 16-channel networks (2 levels, 32 x 32 windows) only";
+    unet_destroy(u);
+    return nullptr;
+  }
   const bool bfm = precision == 1 || precision == 3;
   const bool tfm = precision == 4;
   auto shapes = unet_param_shapes(d);
@@ -2347,7 +2372,7 @@ bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs&
     gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(bsrc, c.n, G, c.u->stats);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     c.u->launches += 1;
-    const TcXf xa{c.u->stats, G, Cg, 0, 1}, xb{c.u->stats, G, Cg, Ca, 1}, xr{};
+    const TcXf xa{c.u->stats, G, Cg, 0, 1}, xb{c.u->stats, G, Cg, Ca, 1};
     for (int py = 0; py < 2; ++py)
       for (int px = 0; px < 2; ++px) {
         TcGeom g;
@@ -2362,8 +2387,7 @@ bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs&
     const bool s2 = conv_run<TA>(c, dw.w1s, b, false, (const float*)lb.T3, (float*)lb.T2, H, nullptr, lb.bT2,
                                  nullptr, nullptr, nullptr, nullptr, &xb);
     gn_stats(c, (const float*)lb.T2, H, cout, s2 ? lb.bT2 : nullptr);
-    conv_run<TA>(c, dw.wska, a, false, nullptr, (float*)lh.T2, Hh, nullptr, nullptr, nullptr, nullptr, nullptr,
-                 nullptr, &xr);
+    conv_run<TA>(c, dw.wska, a, false, nullptr, (float*)lh.T2, Hh);
     const TcXf x2{c.u->stats, G, cout / G, 0, 1};
     TcGeom g2;
     g2.oy = -1;
@@ -2378,9 +2402,16 @@ bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs&
   const double nb = (double)c.n * ((double)Hh * Hh * Ca + (double)H * H * Cb);
   const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (4.0 + wr)) : -1;
   const BlkSrc bsrc{bsa, bsb, Ca, Cb, Hh * Hh / 32, H * H / 32};
+  // the shortcuts' operands: copies of a and b, except for TF32, whose
+  // tensor cores read the raw float32 inputs
+  const bool tfm = std::is_same<TA, tf32>::value;
+  const void* ska = tfm ? (const void*)a : lh.T4;
+  const void* skb = tfm ? (const void*)b : lb.T4;
   gn_finalize_blk_kernel<<<(c.n * G + 3) / 4, 128, 0, c.st>>>(bsrc, c.n, G, c.u->stats);
-  gn_apply_launch<TA>(c, a, Hh * Hh, Ca, true, lh.T1, lh.T4, sp ? lh.T1lo : nullptr, sp ? lh.T4lo : nullptr, Cg, 0);
-  gn_apply_launch<TA>(c, b, H * H, Cb, true, lb.T1, lb.T4, sp ? lb.T1lo : nullptr, sp ? lb.T4lo : nullptr, Cg, Ca);
+  gn_apply_launch<TA>(c, a, Hh * Hh, Ca, true, lh.T1, tfm ? nullptr : lh.T4, sp ? lh.T1lo : nullptr,
+                      sp ? lh.T4lo : nullptr, Cg, 0);
+  gn_apply_launch<TA>(c, b, H * H, Cb, true, lb.T1, tfm ? nullptr : lb.T4, sp ? lb.T1lo : nullptr,
+                      sp ? lb.T4lo : nullptr, Cg, Ca);
   if (c.u->prof) c.u->prof->end(pr, c.st);
   c.u->launches += 3;
   for (int py = 0; py < 2; ++py)
@@ -2398,13 +2429,13 @@ bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs&
                                sp ? lb.T1lo : nullptr, lb.bT2);
   gn<TA>(c, (const float*)lb.T2, H, cout, lb.T1, true, nullptr, sp ? lb.T1lo : nullptr, nullptr,
          s2 ? lb.bT2 : nullptr);
-  conv_run<TA>(c, dw.wska, lh.T4, false, nullptr, (float*)lh.T2, Hh, sp ? lh.T4lo : nullptr);
+  conv_run<TA>(c, dw.wska, ska, false, nullptr, (float*)lh.T2, Hh, sp ? lh.T4lo : nullptr);
   TcGeom g2;
   g2.oy = -1;
   g2.ox = -1;
   g2.res_up = 1;
   *y_stats = conv_run<TA>(c, c2, lb.T1, false, (const float*)lh.T2, Y, H, sp ? lb.T1lo : nullptr, bsY, &dw.wsks,
-                          lb.T4, sp ? lb.T4lo : nullptr, &g2);
+                          skb, sp ? lb.T4lo : nullptr, &g2);
   return true;
 }
 
@@ -2417,7 +2448,10 @@ bool resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
   const ConvW& c2 = c.u->convs[wi++];
   const ConvW* sk = nullptr;
   if (cin != cout) sk = &c.u->convs[wi++];
-  const bool need_copy = sk && !std::is_same<TA, float>::value;
+  // the shortcut's operand: a copy of X in the operand type, except for
+  // TF32, whose tensor cores read the raw float32 X (using its top 19 bits)
+  const bool tfm = std::is_same<TA, tf32>::value;
+  const bool need_copy = sk && !std::is_same<TA, float>::value && !tfm;
   const bool sp = c.u->split;
   if (c.u->fuse_gn && std::is_same<TA, tf32>::value && tc_path<TA>(c1, b.H) && tc_path<TA>(c2, b.H) &&
       (!sk || tc_path<TA>(*sk, b.H)) && gn_stats_ok(c, b.H, cin) && gn_stats_ok(c, b.H, cout)) {
@@ -2438,17 +2472,19 @@ bool resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
          sp && need_copy ? b.T4lo : nullptr, bsX);
   const bool s2 = conv_run<TA>(c, c1, b.T1, false, nullptr, (float*)b.T2, b.H, sp ? b.T1lo : nullptr, b.bT2);
   // the shortcut folds into conv2's K loop when both run on the tensor cores
-  const bool fold = need_copy && tc_path<TA>(c2, b.H) && tc_path<TA>(*sk, b.H);
+  const bool fold = (need_copy || tfm) && sk && tc_path<TA>(c2, b.H) && tc_path<TA>(*sk, b.H);
+  const void* skx = tfm ? (const void*)X : b.T4;  // the shortcut's operand
   const float* res = X;
   if (sk && !fold) {
-    if (need_copy) conv_run<TA>(c, *sk, b.T4, false, nullptr, (float*)b.T3, b.H, sp ? b.T4lo : nullptr);
+    if (need_copy || (tfm && tc_path<TA>(*sk, b.H)))
+      conv_run<TA>(c, *sk, skx, false, nullptr, (float*)b.T3, b.H, sp ? b.T4lo : nullptr);
     else conv_run<TA>(c, *sk, X, true, nullptr, (float*)b.T3, b.H);
     res = (const float*)b.T3;
   }
   gn<TA>(c, (const float*)b.T2, b.H, cout, b.T1, true, nullptr, sp ? b.T1lo : nullptr, nullptr,
          s2 ? b.bT2 : nullptr);
   if (fold)
-    return conv_run<TA>(c, c2, b.T1, false, nullptr, Y, b.H, sp ? b.T1lo : nullptr, bsY, sk, b.T4,
+    return conv_run<TA>(c, c2, b.T1, false, nullptr, Y, b.H, sp ? b.T1lo : nullptr, bsY, sk, skx,
                         sp ? b.T4lo : nullptr);
   return conv_run<TA>(c, c2, b.T1, false, res, Y, b.H, sp ? b.T1lo : nullptr, bsY);
 }
@@ -2575,6 +2611,25 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
     return false;
   }
   if (n <= 0) return true;
+  if (u->small) {
+    // algorithmic FLOPs of the network (convolutions over the materialised
+    // concat, 2 per multiply-add); bytes: the input windows and F
+    const UNetDesc& d = u->d;
+    double fl = 2.0 * 1024 * 9 * d.in_ch * 16;                       // input conv
+    fl += 2.0 * 1024 * (2 * 9 * 16 * 16) + 2.0 * 256 * (4 * 9 * 16 * 16);  // encoder, bottom
+    fl += 2.0 * 1024 * (9 * 32 * 16 + 9 * 16 * 16 + 32 * 16);       // decoder block
+    fl += 2.0 * 1024 * 9 * 16;                                       // output conv
+    const int pr = u->prof ? u->prof->begin(PK_CONV_TC, st, fl * n, (double)n * 1024 * 4 * (d.in_ch + 1)) : -1;
+    std::string e;
+    const bool ok = small_net_forward(u->small, x_in, n, F, u->status, u->wait_limit, st, &e);
+    if (u->prof) u->prof->end(pr, st);
+    u->launches++;
+    if (!ok) {
+      err->code = 3;
+      err->msg = "small UNet: " + e;
+    }
+    return ok;
+  }
   if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err);
   if (u->precision == 4) return forward_t<tf32>(u, x_in, n, F, st, err);
   return forward_t<float>(u, x_in, n, F, st, err);

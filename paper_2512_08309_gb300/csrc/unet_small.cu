@@ -1,0 +1,870 @@
+// Fused per-window UNet of the 16-channel networks on the sm_103a tensor
+// cores: the window denoiser F (Sec. 5.3) of the single-level synthetic
+// stacks -- 2 resolution levels of 16 channels, 32 x 32 windows,
+// GroupNorm(4), SiLU, no attention -- with every 3x3 / 1x1 convolution on
+// tcgen05 in BF16 (kind::f16) or FP8 E4M3 (kind::f8f6f4, per-output-channel
+// weight scales, power-of-two activation scales) and FP32 accumulation in
+// tensor memory.
+//
+// One CTA evaluates one window at a time (persistent over the batch) and
+// keeps the whole network on chip; only the input window and F touch HBM.
+//
+//   Slots.  A level's activations live as 128-row TMEM accumulators whose
+//     rows are "slots" of a zero-padded image with rows of WP slots (WP =
+//     40 at 32 x 32, 24 at 16 x 16): slot (y + 1) * WP + (x + 1) holds pixel
+//     (y, x); the extra columns are padding.  Output M tiles are 128
+//     consecutive slots, so the slot of tap (dy, dx) of every row of a tile
+//     is that row's slot + dy * WP + dx: one uniform shift.  The operand of
+//     a convolution is therefore the previous tensor written once into
+//     shared memory in the same slot order (K-major, no swizzle, 16-byte
+//     "planes" of channels per slot), and each tap is one UMMA descriptor
+//     into it -- no im2col copy.  Padding slots hold zeros; the results in
+//     padding rows of the accumulators are never read.  10 M tiles cover
+//     32 x 32 (1280 slots for 1024 pixels), 3 tiles cover 16 x 16.
+//   Planes.  A plane is 16 bytes per slot: 8 bf16 or 16 E4M3 channels.  One
+//     MMA takes 32 bytes of K per row (16 bf16 / 32 E4M3): for BF16 the two
+//     halves of a 16-channel tap are two planes (LBO = plane stride); for
+//     FP8 with 16 channels two taps share one MMA (the second K half is the
+//     same plane shifted by the taps' slot distance, LBO = that distance;
+//     the ninth tap pairs with zero weights).
+//   GroupNorm.  Statistics of a tensor come from TMEM in two passes over
+//     its valid slots (mean, then squared deviations; FP32, block-reduced);
+//     the operand builder then writes silu((x - mean) * rstd) quantized into
+//     the planes.  ResBlock sums (residual, shortcut) are explicit FP32
+//     passes over TMEM, so every accumulator holds one convolution and its
+//     per-channel dequantisation scale applies when it is read.
+//   Warps.  8 warps; warp w reads and writes TMEM lanes 32 (w % 4) .. + 31 of
+//     every other M tile; thread 0 issues the MMAs and commits them to one
+//     mbarrier that every thread waits on (bounded: a wait that runs out
+//     sets the status word; the CTA then stops at the next block-wide vote,
+//     frees its TMEM and returns).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace idf {
+namespace {
+
+constexpr int SC = 16;                 // channels of both levels
+constexpr int WP0 = 40, WP1 = 24;      // slots per padded row
+constexpr int MT0 = 10, MT1 = 3;       // 128-slot M tiles
+constexpr int PL0 = 1376, PL1 = 448;   // slots per operand plane, margins included
+constexpr int MARG = 8;                // margin slots before slot 0 of a plane
+constexpr int NTHR = 256;
+constexpr int NPLANE = 4;              // planes of the operand buffer (32 bf16 channels)
+constexpr int OPB_BYTES = NPLANE * PL0 * 16;
+constexpr int BLK = 512;               // bytes of one MMA's weight block (16 rows x 32 bytes)
+// weight blocks per convolution: 9 taps (bf16, 16 channels), 5 tap pairs
+// (fp8, 16 channels), x 2 for the 32-channel convolution in bf16
+constexpr int NCONV = 10;              // tensor-core convolutions (all but the input conv)
+constexpr uint32_t TM_A = 0, TM_B = 160, TM_C = 320, TM_D = 368, TM_E = 320;
+constexpr float ACT_SCALE = 32.0f;     // FP8: normalised operands are quantised as z * 32
+
+// convolution indices into the weight and scale tables
+enum { CV_E0A = 0, CV_E0B, CV_E1A, CV_E1B, CV_MA, CV_MB, CV_D1, CV_D2, CV_SK, CV_OUT };
+
+struct SmallArgs {
+  const float* x;          // [n][32][32][in_ch] float32 (NHWC)
+  float* F;                // [n][32][32] float32
+  const uint8_t* wblk;     // weight blocks, convolution after convolution
+  const int* wofs;         // [NCONV] first block of each convolution
+  const float* dqw;        // [NCONV][16] weight dequantisation scales
+  const float* w_in;       // [9][in_ch][16] input convolution, float32
+  int n, in_ch, fp8, n_blocks;
+  int* status;
+  long long wait_limit;
+};
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// f32 accumulator, A and B of one type (bf16 = 1 under kind::f16, E4M3 = 0
+// under kind::f8f6f4), both K-major, N = 16, M = 128
+__host__ __device__ constexpr uint32_t idesc16(bool fp8) {
+  return (1u << 4) | ((fp8 ? 0u : 1u) << 7) | ((fp8 ? 0u : 1u) << 10) | ((uint32_t)(16 >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma16(uint32_t d, uint64_t a, uint64_t b, bool fp8, uint32_t acc) {
+  if (fp8)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc16(true)), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc16(false)), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tst16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+// one level's slot geometry
+struct Geo {
+  int WP, MT, PL, H;
+  __device__ int first() const { return WP; }  // slot of pixel (0, -1): row 1, column 0
+};
+__device__ __forceinline__ Geo geo(int lv) { return lv == 0 ? Geo{WP0, MT0, PL0, 32} : Geo{WP1, MT1, PL1, 16}; }
+
+// 16 values -> 16 bytes of E4M3 (value i in byte i)
+__device__ __forceinline__ uint4 pack_e4m3(const float (&v)[16], int base) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[base + 4 * k], v[base + 4 * k + 1]),
+                                                             __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+        make_float2(v[base + 4 * k + 2], v[base + 4 * k + 3]), __NV_SATFINITE, __NV_E4M3);
+    w[k] = (uint32_t)lo | ((uint32_t)hi << 16);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ uint4 pack_bf16(const float (&v)[16], int base) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[base + 2 * k], v[base + 2 * k + 1]);
+    w[k] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Write 16 channel values of one slot into the operand planes starting at
+// plane p0: bf16 -> planes p0 (channels 0-7), p0 + 1 (8-15); fp8 -> plane p0.
+__device__ __forceinline__ void put16(uint8_t* opb, int PL, int p0, int slot, const float (&v)[16], bool fp8) {
+  const size_t o = (size_t)(slot + MARG) * 16;
+  if (fp8) {
+    *reinterpret_cast<uint4*>(opb + (size_t)p0 * PL * 16 + o) = pack_e4m3(v, 0);
+  } else {
+    *reinterpret_cast<uint4*>(opb + (size_t)p0 * PL * 16 + o) = pack_bf16(v, 0);
+    *reinterpret_cast<uint4*>(opb + (size_t)(p0 + 1) * PL * 16 + o) = pack_bf16(v, 8);
+  }
+}
+
+// zero the slots of planes [0, np) that no M tile owns (top / bottom padding
+// rows and the margins)
+__device__ void zero_unowned(uint8_t* opb, const Geo& g, int np) {
+  const int lo = g.first() + MARG;                 // planes' slot index of the first owned slot
+  const int hi = g.first() + 128 * g.MT + MARG;    // one past the last owned
+  const int per = lo + (g.PL - hi);
+  for (int i = threadIdx.x; i < np * per; i += NTHR) {
+    const int p = i / per, k = i % per;
+    const int idx = k < lo ? k : hi + (k - lo);
+    *reinterpret_cast<uint4*>(opb + ((size_t)p * g.PL + idx) * 16) = make_uint4(0, 0, 0, 0);
+  }
+}
+
+// block-wide sums of NV values per thread (result in every thread's out)
+template <int NV>
+__device__ void block_sum(float (&v)[NV], float* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp * NV + k] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NTHR / 32; ++w) s += red[w * NV + k];
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(s_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+__global__ void __launch_bounds__(NTHR, 1) unet16_kernel(SmallArgs a) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  uint8_t* opb = dsm;                                       // operand planes (and fp32 scratch)
+  uint8_t* wsm = dsm + OPB_BYTES;                           // weight blocks
+  float* up = reinterpret_cast<float*>(wsm + (size_t)a.n_blocks * BLK);  // [16][16][16] h for the upsampling
+  float* dqs = up + 16 * 16 * 16;                           // [NCONV][16] weight scales
+  float* win = dqs + NCONV * 16;                            // [9][in_ch][16] input conv
+  float* red = win + 9 * 2 * 16;                            // [8 warps][8] reductions
+  float* stt = red + 64;                                    // [8] mean, [8] rstd
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_sh;
+
+  __shared__ int skip_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, half = warp >> 2;
+  const bool fp8 = a.fp8 != 0;
+  // once a bounded wait of any launch has run out, later CTAs return at once
+  // (one thread reads the word so that the whole CTA decides alike)
+  if (tid == 0) skip_sh = *(volatile int*)a.status;
+  __syncthreads();
+  if (skip_sh) return;
+
+  // stage the weights once per CTA
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.wblk);
+    uint4* dst = reinterpret_cast<uint4*>(wsm);
+    for (int i = tid; i < a.n_blocks * BLK / 16; i += NTHR) dst[i] = src[i];
+    for (int i = tid; i < NCONV * 16; i += NTHR) dqs[i] = a.dqw[i];
+    for (int i = tid; i < 9 * a.in_ch * 16; i += NTHR) win[i] = a.w_in[i];
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(s_u32(&tmem_sh))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+  const uint32_t opb_a = s_u32(opb), wsm_a = s_u32(wsm);
+  uint32_t phase = 0;
+  bool alive = true;
+
+  // --- helpers ------------------------------------------------------------
+  // thread-owned slots of a level: M tiles m = half, half + 2, ...; row 32 q + lane
+  auto slot_of = [&](const Geo& g, int m) { return g.first() + 128 * m + 32 * q + lane; };
+  auto valid = [&](const Geo& g, int s) {
+    const int c = s % g.WP;
+    return c >= 1 && c <= g.H;
+  };
+  // commit the MMAs issued so far by thread 0 and wait for them (all threads)
+  auto sync_mma = [&]() -> bool {
+    if (tid == 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       s_u32(&mbar))
+                   : "memory");
+    bool ok = mbar_wait(&mbar, phase & 1u, a.wait_limit);
+    phase++;
+    if (!ok) atomicExch(a.status, 1);
+    ok = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return ok;
+  };
+  // make operand writes and TMEM reads of every thread visible before MMAs
+  auto before_mma = [&]() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+  // 3x3 convolution of the operand planes (16 channels, or 32 with cin32)
+  // into accumulator columns dst, 16 per M tile (thread 0 only)
+  auto conv3 = [&](const Geo& g, int cv, bool cin32, uint32_t dst) {
+    const uint32_t plb = (uint32_t)g.PL * 16;
+    const uint32_t w0 = wsm_a + (uint32_t)a.wofs[cv] * BLK;
+    for (int m = 0; m < g.MT; ++m) {
+      const uint32_t d = tmem + dst + 16 * m;
+      const int s0 = g.first() + 128 * m + MARG;
+      if (!fp8) {
+        const int kp = cin32 ? 2 : 1;
+        for (int t = 0; t < 9; ++t) {
+          const int o = (t / 3 - 1) * g.WP + (t % 3 - 1);
+          for (int k = 0; k < kp; ++k)
+            mma16(d, sdesc(opb_a + (uint32_t)(2 * k) * plb + (uint32_t)(s0 + o) * 16, plb, 128),
+                  sdesc(w0 + (uint32_t)(t * kp + k) * BLK, 256, 128), false, (t | k) ? 1u : 0u);
+        }
+      } else if (cin32) {
+        for (int t = 0; t < 9; ++t) {
+          const int o = (t / 3 - 1) * g.WP + (t % 3 - 1);
+          mma16(d, sdesc(opb_a + (uint32_t)(s0 + o) * 16, plb, 128), sdesc(w0 + (uint32_t)t * BLK, 256, 128),
+                true, t ? 1u : 0u);
+        }
+      } else {
+        for (int pi = 0; pi < 5; ++pi) {
+          const int t1 = 2 * pi, t2 = 2 * pi + 1;
+          const int o1 = (t1 / 3 - 1) * g.WP + (t1 % 3 - 1);
+          const int o2 = t2 < 9 ? (t2 / 3 - 1) * g.WP + (t2 % 3 - 1) : o1 + 1;
+          mma16(d, sdesc(opb_a + (uint32_t)(s0 + o1) * 16, (uint32_t)(o2 - o1) * 16, 128),
+                sdesc(w0 + (uint32_t)pi * BLK, 256, 128), true, pi ? 1u : 0u);
+        }
+      }
+    }
+  };
+  // 1x1 convolution of the 32-channel operand (the decoder shortcut)
+  auto conv1 = [&](const Geo& g, int cv, uint32_t dst) {
+    const uint32_t plb = (uint32_t)g.PL * 16;
+    const uint32_t w0 = wsm_a + (uint32_t)a.wofs[cv] * BLK;
+    for (int m = 0; m < g.MT; ++m) {
+      const uint32_t d = tmem + dst + 16 * m;
+      const int s0 = g.first() + 128 * m + MARG;
+      if (!fp8) {
+        for (int k = 0; k < 2; ++k)
+          mma16(d, sdesc(opb_a + (uint32_t)(2 * k) * plb + (uint32_t)s0 * 16, plb, 128),
+                sdesc(w0 + (uint32_t)k * BLK, 256, 128), false, k ? 1u : 0u);
+      } else {
+        mma16(d, sdesc(opb_a + (uint32_t)s0 * 16, plb, 128), sdesc(w0, 256, 128), true, 0u);
+      }
+    }
+  };
+  // GroupNorm statistics (4 groups of 4 channels) of accumulator region src
+  // at level g, values scaled by dq; result in stt[0..3] (mean), stt[4..7]
+  auto gn_stats16 = [&](const Geo& g, uint32_t src, const float* dq) {
+    float s[4] = {0, 0, 0, 0};
+    for (int m = half; m < g.MT; m += 2) {
+      float v[16];
+      tld16(tmem + lane_off + src + 16 * m, v);
+      if (!valid(g, slot_of(g, m))) continue;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) s[c >> 2] += v[c] * dq[c];
+    }
+    block_sum<4>(s, red);
+    const float inv = 1.0f / (4.0f * g.H * g.H);
+    float mu[4], d2[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mu[k] = s[k] * inv;
+    for (int m = half; m < g.MT; m += 2) {
+      float v[16];
+      tld16(tmem + lane_off + src + 16 * m, v);
+      if (!valid(g, slot_of(g, m))) continue;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float e = v[c] * dq[c] - mu[c >> 2];
+        d2[c >> 2] += e * e;
+      }
+    }
+    block_sum<4>(d2, red);
+    if (tid < 4) {
+      stt[tid] = mu[tid];
+      stt[4 + tid] = rsqrtf(d2[tid] * inv + 1e-5f);
+    }
+    __syncthreads();
+  };
+  // operand of a 16-channel tensor: silu(gn(x)) quantised into planes 0..
+  auto build16 = [&](const Geo& g, uint32_t src, const float* dq) {
+    zero_unowned(opb, g, fp8 ? 1 : 2);
+    const float sc = fp8 ? ACT_SCALE : 1.0f;
+    for (int m = half; m < g.MT; m += 2) {
+      const int s = slot_of(g, m);
+      float v[16];
+      tld16(tmem + lane_off + src + 16 * m, v);
+      if (valid(g, s)) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = silu((v[c] * dq[c] - stt[c >> 2]) * stt[4 + (c >> 2)]) * sc;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+      }
+      put16(opb, g.PL, 0, s, v, fp8);
+    }
+  };
+  // dst = dst * dq_d + src * dq_s over a level's owned rows (true units out)
+  auto combine = [&](const Geo& g, uint32_t dst, const float* dqd, uint32_t src, const float* dqs_) {
+    for (int m = half; m < g.MT; m += 2) {
+      float v[16], w[16];
+      tld16(tmem + lane_off + dst + 16 * m, v);
+      tld16(tmem + lane_off + src + 16 * m, w);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = v[c] * (dqd ? dqd[c] : 1.0f) + w[c] * dqs_[c];
+      tst16(tmem + lane_off + dst + 16 * m, v);
+    }
+  };
+  // ResBlock(16 -> 16) on region X (true units) with temporary region T
+  auto resblock = [&](const Geo& g, uint32_t X, uint32_t T, int cva, int cvb) -> bool {
+    const float one[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+    gn_stats16(g, X, one);
+    build16(g, X, one);
+    before_mma();
+    if (tid == 0) conv3(g, cva, false, T);
+    if (!sync_mma()) return false;
+    gn_stats16(g, T, dqs + 16 * cva);
+    build16(g, T, dqs + 16 * cva);
+    before_mma();
+    if (tid == 0) conv3(g, cvb, false, T);
+    if (!sync_mma()) return false;
+    combine(g, X, nullptr, T, dqs + 16 * cvb);
+    return true;
+  };
+
+  const Geo g0 = geo(0), g1 = geo(1);
+  for (int wi = blockIdx.x; wi < a.n && alive; wi += gridDim.x) {
+    const float* xw = a.x + (size_t)wi * 32 * 32 * a.in_ch;
+    // input convolution (float32, SIMT) into A
+    for (int m = half; m < MT0; m += 2) {
+      const int s = slot_of(g0, m);
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+      if (valid(g0, s)) {
+        const int y = s / WP0 - 1, x = s % WP0 - 1;
+        for (int t = 0; t < 9; ++t) {
+          const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+          if (yy < 0 || yy >= 32 || xx < 0 || xx >= 32) continue;
+          for (int ci = 0; ci < a.in_ch; ++ci) {
+            const float xv = xw[(yy * 32 + xx) * a.in_ch + ci];
+            const float* wr = win + (t * a.in_ch + ci) * 16;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = fmaf(xv, wr[c], v[c]);
+          }
+        }
+      }
+      tst16(tmem + lane_off + TM_A + 16 * m, v);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // encoder level 0: A = ResBlock(A) (the skip)
+    if (!(alive = resblock(g0, TM_A, TM_B, CV_E0A, CV_E0B))) break;
+    // 2x2 average pool of A into C through fp32 scratch in the operand buffer
+    {
+      float* scr = reinterpret_cast<float*>(opb);
+      for (int m = half; m < MT0; m += 2) {
+        const int s = slot_of(g0, m);
+        float v[16];
+        tld16(tmem + lane_off + TM_A + 16 * m, v);
+        if (!valid(g0, s)) continue;
+        const int y = s / WP0 - 1, x = s % WP0 - 1;
+        float4* d = reinterpret_cast<float4*>(scr + (y * 32 + x) * 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      }
+      __syncthreads();
+      for (int m = half; m < MT1; m += 2) {
+        const int s = slot_of(g1, m);
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+        if (valid(g1, s)) {
+          const int y = s / WP1 - 1, x = s % WP1 - 1;
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            v[c] = 0.25f * ((scr[((2 * y) * 32 + 2 * x) * 16 + c] + scr[((2 * y) * 32 + 2 * x + 1) * 16 + c]) +
+                            (scr[((2 * y + 1) * 32 + 2 * x) * 16 + c] + scr[((2 * y + 1) * 32 + 2 * x + 1) * 16 + c]));
+        }
+        tst16(tmem + lane_off + TM_C + 16 * m, v);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    // encoder level 1 and the bottom block at 16 x 16
+    if (!(alive = resblock(g1, TM_C, TM_D, CV_E1A, CV_E1B))) break;
+    if (!(alive = resblock(g1, TM_C, TM_D, CV_MA, CV_MB))) break;
+    // decoder: [up2(h), skip] with h in C, skip in A
+    {
+      for (int m = half; m < MT1; m += 2) {
+        const int s = slot_of(g1, m);
+        float v[16];
+        tld16(tmem + lane_off + TM_C + 16 * m, v);
+        if (!valid(g1, s)) continue;
+        const int y = s / WP1 - 1, x = s % WP1 - 1;
+        float4* d = reinterpret_cast<float4*>(up + (y * 16 + x) * 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      }
+      __syncthreads();
+      // concat statistics, 4 groups of 8: groups 0-1 from h (upsampling
+      // repeats each value 4 times: same mean and variance), 2-3 from skip;
+      // and (FP8) the largest magnitude of the raw concat
+      float s8[4] = {0, 0, 0, 0};
+      float amax = 0.0f;
+      for (int i = tid; i < 16 * 16; i += NTHR)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          s8[c >> 3] += up[i * 16 + c];
+          amax = fmaxf(amax, fabsf(up[i * 16 + c]));
+        }
+      for (int m = half; m < MT0; m += 2) {
+        float v[16];
+        tld16(tmem + lane_off + TM_A + 16 * m, v);
+        if (!valid(g0, slot_of(g0, m))) continue;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          s8[2 + (c >> 3)] += v[c];
+          amax = fmaxf(amax, fabsf(v[c]));
+        }
+      }
+      block_sum<4>(s8, red);
+      float mu[4];
+      mu[0] = s8[0] / 2048.0f;  // 256 px x 8 channels
+      mu[1] = s8[1] / 2048.0f;
+      mu[2] = s8[2] / 8192.0f;  // 1024 px x 8 channels
+      mu[3] = s8[3] / 8192.0f;
+      float d2[4] = {0, 0, 0, 0};
+      for (int i = tid; i < 16 * 16; i += NTHR)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float e = up[i * 16 + c] - mu[c >> 3];
+          d2[c >> 3] += e * e;
+        }
+      for (int m = half; m < MT0; m += 2) {
+        float v[16];
+        tld16(tmem + lane_off + TM_A + 16 * m, v);
+        if (!valid(g0, slot_of(g0, m))) continue;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float e = v[c] - mu[2 + (c >> 3)];
+          d2[2 + (c >> 3)] += e * e;
+        }
+      }
+      block_sum<4>(d2, red);
+      // block maximum of amax (through the reduction scratch)
+      {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (lane == 0) red[warp] = amax;
+        __syncthreads();
+        amax = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NTHR / 32; ++w) amax = fmaxf(amax, red[w]);
+        __syncthreads();
+      }
+      float rs[4];
+      rs[0] = rsqrtf(d2[0] / 2048.0f + 1e-5f);
+      rs[1] = rsqrtf(d2[1] / 2048.0f + 1e-5f);
+      rs[2] = rsqrtf(d2[2] / 8192.0f + 1e-5f);
+      rs[3] = rsqrtf(d2[3] / 8192.0f + 1e-5f);
+      // FP8: the raw concat is quantised as x / s_raw, s_raw a power of two
+      // that maps the largest magnitude into E4M3's range
+      const float s_raw = (fp8 && amax > 0.0f) ? exp2f(ceilf(log2f(amax / 448.0f))) : 1.0f;
+      // (1) raw concat -> 1x1 shortcut into B
+      for (int pass = 0; pass < 2; ++pass) {
+        zero_unowned(opb, g0, fp8 ? 2 : 4);
+        for (int m = half; m < MT0; m += 2) {
+          const int s = slot_of(g0, m);
+          float sk[16], uh[16];
+          tld16(tmem + lane_off + TM_A + 16 * m, sk);
+          if (valid(g0, s)) {
+            const int y = s / WP0 - 1, x = s % WP0 - 1;
+            const float* u = up + ((y >> 1) * 16 + (x >> 1)) * 16;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) uh[c] = u[c];
+            if (pass == 0) {
+              const float inv = 1.0f / s_raw;
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                uh[c] *= inv;
+                sk[c] *= inv;
+              }
+            } else {
+              const float sc = fp8 ? ACT_SCALE : 1.0f;
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                uh[c] = silu((uh[c] - mu[c >> 3]) * rs[c >> 3]) * sc;
+                sk[c] = silu((sk[c] - mu[2 + (c >> 3)]) * rs[2 + (c >> 3)]) * sc;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) uh[c] = sk[c] = 0.0f;
+          }
+          put16(opb, PL0, 0, s, uh, fp8);
+          put16(opb, PL0, fp8 ? 1 : 2, s, sk, fp8);
+        }
+        before_mma();
+        if (tid == 0) {
+          if (pass == 0) conv1(g0, CV_SK, TM_B);
+          else conv3(g0, CV_D1, true, TM_A);
+        }
+        if (!(alive = sync_mma())) break;
+      }
+      if (!alive) break;
+      // (2) conv2 of silu(gn(conv1)) into E; B = shortcut + conv2
+      gn_stats16(g0, TM_A, dqs + 16 * CV_D1);
+      build16(g0, TM_A, dqs + 16 * CV_D1);
+      before_mma();
+      if (tid == 0) conv3(g0, CV_D2, false, TM_E);
+      if (!(alive = sync_mma())) break;
+      float dsk[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) dsk[c] = dqs[16 * CV_SK + c] * s_raw;
+      combine(g0, TM_B, dsk, TM_E, dqs + 16 * CV_D2);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    // output head: conv3x3(silu(gn(B))) (one real output channel) into A
+    {
+      const float one[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+      gn_stats16(g0, TM_B, one);
+      build16(g0, TM_B, one);
+      before_mma();
+      if (tid == 0) conv3(g0, CV_OUT, false, TM_A);
+      if (!(alive = sync_mma())) break;
+      float* Fw = a.F + (size_t)wi * 32 * 32;
+      const float dq0 = dqs[16 * CV_OUT];
+      for (int m = half; m < MT0; m += 2) {
+        const int s = slot_of(g0, m);
+        float v[16];
+        tld16(tmem + lane_off + TM_A + 16 * m, v);
+        if (!valid(g0, s)) continue;
+        Fw[(s / WP0 - 1) * 32 + (s % WP0 - 1)] = v[0] * dq0;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+  }
+  if (!alive && tid == 0) {
+    // let any MMA still in flight finish before the columns are freed
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(&mbar))
+                 : "memory");
+    mbar_wait(&mbar, phase & 1u, a.wait_limit);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+// round to the nearest E4M3 value (ties to even), |v| <= 448; returns the
+// byte: sign, 4 exponent bits (bias 7), 3 mantissa bits, subnormals 2^-9 m
+uint8_t e4m3_rn(double v) {
+  const uint8_t sg = v < 0 ? 0x80 : 0;
+  double x = fabs(v);
+  if (x == 0.0) return sg;
+  if (x >= 448.0) return sg | 0x7E;
+  int e;
+  frexp(x, &e);
+  e -= 1;  // x in [2^e, 2^(e+1))
+  if (e < -6) {
+    const double m = nearbyint(x / ldexp(1.0, -9));  // subnormal quantum 2^-9
+    if (m >= 8.0) return sg | 0x08;                 // rounds up to 2^-6
+    return sg | (uint8_t)m;
+  }
+  double m = nearbyint(x / ldexp(1.0, e - 3));       // 8 .. 16
+  if (m >= 16.0) {
+    m = 8.0;
+    e += 1;
+  }
+  if (e > 8 || (e == 8 && m > 14.0)) return sg | 0x7E;
+  return sg | (uint8_t)(((e + 7) << 3) | ((int)m - 8));
+}
+
+uint16_t bf16_rn_host(float v) {
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+}  // namespace
+
+struct SmallNet {
+  uint8_t* wblk = nullptr;
+  int* wofs = nullptr;
+  float* dqw = nullptr;
+  float* w_in = nullptr;
+  int n_blocks = 0, in_ch = 1, fp8 = 0;
+};
+
+bool small_net_eligible(const UNetDesc& d) {
+  return d.levels == 2 && d.ch.size() == 2 && d.ch[0] == SC && d.ch[1] == SC && d.window == 32 && !d.attn &&
+         d.groups == 4 && d.out_ch == 1 && (d.in_ch == 1 || d.in_ch == 2);
+}
+
+// Pack the weights (declaration order: in_conv; enc0 conv1, conv2; enc1
+// conv1, conv2; bottom conv1, conv2; dec0 conv1 (32 -> 16), conv2, skip
+// (1x1, 32 -> 16); out_conv (1 <- 16)) into MMA blocks.  A block is 16
+// output-channel rows x 32 bytes of K as four 8-row x 16-byte core
+// matrices: (k half, row group) at (2 k + g) * 128 bytes.
+SmallNet* small_net_create(const UNetDesc& d, const float* w, bool fp8, Err* err) {
+  auto shapes = unet_param_shapes(d);
+  std::vector<size_t> off(shapes.size() + 1, 0);
+  for (size_t i = 0; i < shapes.size(); ++i)
+    off[i + 1] = off[i] + (size_t)shapes[i][0] * shapes[i][1] * shapes[i][2] * shapes[i][3];
+  // tensor index of each tensor-core convolution
+  const int tix[NCONV] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10};
+  std::vector<uint8_t> blk;
+  std::vector<int> wofs(NCONV);
+  std::vector<float> dq(NCONV * 16, 1.0f);
+  for (int cv = 0; cv < NCONV; ++cv) {
+    const auto& sh = shapes[tix[cv]];
+    const int co = sh[0], ci = sh[1], ks = sh[2], taps = ks * ks;
+    const float* src = w + off[tix[cv]];
+    auto W = [&](int n, int c, int t) -> double {  // weight of output n, input c, tap t (0 beyond)
+      if (n >= co || c >= ci || t >= taps) return 0.0;
+      return src[((size_t)n * ci + c) * taps + t];
+    };
+    float s[16];
+    for (int n = 0; n < 16; ++n) {
+      double mx = 0.0;
+      for (int c = 0; c < ci; ++c)
+        for (int t = 0; t < taps; ++t) mx = std::max(mx, fabs(W(n, c, t)));
+      s[n] = (fp8 && mx > 0.0) ? (float)(mx / 448.0) : 1.0f;
+      // normalised FP8 operands are quantised as z * ACT_SCALE; the shortcut's
+      // raw operand carries its own per-window scale, applied in the kernel
+      dq[cv * 16 + n] = fp8 ? (cv == CV_SK ? s[n] : s[n] / ACT_SCALE) : 1.0f;
+    }
+    wofs[cv] = (int)(blk.size() / BLK);
+    // K bytes of one block: kh = 0, 1 halves of 16 bytes; element e of half kh
+    auto put_block = [&](auto elem) {  // elem(n, kh, e) -> value (already scaled for fp8)
+      const size_t b0 = blk.size();
+      blk.resize(b0 + BLK, 0);
+      for (int kh = 0; kh < 2; ++kh)
+        for (int g = 0; g < 2; ++g)
+          for (int r = 0; r < 8; ++r) {
+            const int n = 8 * g + r;
+            uint8_t* row = &blk[b0 + (size_t)(2 * kh + g) * 128 + (size_t)r * 16];
+            if (fp8) {
+              for (int e = 0; e < 16; ++e) row[e] = e4m3_rn(elem(n, kh, e) / s[n]);
+            } else {
+              for (int e = 0; e < 8; ++e) {
+                const uint16_t h = bf16_rn_host((float)elem(n, kh, e));
+                memcpy(row + 2 * e, &h, 2);
+              }
+            }
+          }
+    };
+    if (ks == 1) {
+      // 1x1 over 32 channels: bf16 two blocks (16 channels each), fp8 one
+      if (!fp8) {
+        for (int k = 0; k < 2; ++k) put_block([&](int n, int kh, int e) { return W(n, 16 * k + 8 * kh + e, 0); });
+      } else {
+        put_block([&](int n, int kh, int e) { return W(n, 16 * kh + e, 0); });
+      }
+    } else if (!fp8) {
+      const int kp = ci / 16;
+      for (int t = 0; t < 9; ++t)
+        for (int k = 0; k < kp; ++k)
+          put_block([&](int n, int kh, int e) { return W(n, 16 * k + 8 * kh + e, t); });
+    } else if (ci == 32) {
+      for (int t = 0; t < 9; ++t) put_block([&](int n, int kh, int e) { return W(n, 16 * kh + e, t); });
+    } else {
+      for (int pi = 0; pi < 5; ++pi)
+        put_block([&](int n, int kh, int e) { return W(n, e, 2 * pi + kh); });  // tap 9: zero
+    }
+  }
+  // input convolution [tap][ci][16]
+  const int ci0 = shapes[0][1];
+  std::vector<float> win(9 * ci0 * 16);
+  for (int t = 0; t < 9; ++t)
+    for (int c = 0; c < ci0; ++c)
+      for (int n = 0; n < 16; ++n) win[(t * ci0 + c) * 16 + n] = w[((size_t)n * ci0 + c) * 9 + t];
+  SmallNet* s = new SmallNet();
+  s->n_blocks = (int)(blk.size() / BLK);
+  s->in_ch = ci0;
+  s->fp8 = fp8 ? 1 : 0;
+  auto fail = [&](const char* m) {
+    err->code = 2;
+    err->msg = m;
+    small_net_destroy(s);
+    return (SmallNet*)nullptr;
+  };
+  if (cudaMalloc(&s->wblk, blk.size()) != cudaSuccess || cudaMalloc(&s->wofs, NCONV * 4) != cudaSuccess ||
+      cudaMalloc(&s->dqw, dq.size() * 4) != cudaSuccess || cudaMalloc(&s->w_in, win.size() * 4) != cudaSuccess)
+    return fail("cudaMalloc small UNet weights");
+  if (cudaMemcpy(s->wblk, blk.data(), blk.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->wofs, wofs.data(), NCONV * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->dqw, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->w_in, win.data(), win.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail("copy small UNet weights");
+  return s;
+}
+
+void small_net_destroy(SmallNet* s) {
+  if (!s) return;
+  cudaFree(s->wblk);
+  cudaFree(s->wofs);
+  cudaFree(s->dqw);
+  cudaFree(s->w_in);
+  delete s;
+}
+
+// F (n windows, 32 x 32) of x (n, 32, 32, in_ch) NHWC float32
+bool small_net_forward(const SmallNet* s, const float* x, int n, float* F, int* status, long long wait_limit,
+                       cudaStream_t st, std::string* err) {
+  if (n <= 0) return true;
+  const size_t smem = (size_t)OPB_BYTES + (size_t)s->n_blocks * BLK +
+                      (16 * 16 * 16 + NCONV * 16 + 9 * 2 * 16 + 64 + 8) * sizeof(float);
+  static int attr_set = 0;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(unet16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)) !=
+        cudaSuccess) {
+      *err = "cudaFuncSetAttribute (small UNet)";
+      return false;
+    }
+    attr_set = 1;
+  }
+  if (smem > 200 * 1024) {
+    *err = "small UNet shared memory";
+    return false;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SmallArgs a;
+  a.x = x;
+  a.F = F;
+  a.wblk = s->wblk;
+  a.wofs = s->wofs;
+  a.dqw = s->dqw;
+  a.w_in = s->w_in;
+  a.n = n;
+  a.in_ch = s->in_ch;
+  a.fp8 = s->fp8;
+  a.n_blocks = s->n_blocks;
+  a.status = status;
+  a.wait_limit = wait_limit > 0 ? wait_limit : 1000000000LL;
+  unet16_kernel<<<std::min(n, sms), NTHR, smem, st>>>(a);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace idf

@@ -800,8 +800,7 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
   if (!out) return IDF_EINVAL;
   *out = nullptr;
   if (!stack || !opts || stack->n_levels < 1 || stack->n_levels > 2 || !stack->level) return IDF_EINVAL;
-  if (opts->precision == IDF_FP8_E4M3) return IDF_EUNSUPPORTED;
-  if (opts->precision != IDF_FP32 && opts->precision != IDF_BF16 && opts->precision != IDF_BF16X3 &&
+  if (opts->precision != IDF_FP8_E4M3 && opts->precision != IDF_FP32 && opts->precision != IDF_BF16 && opts->precision != IDF_BF16X3 &&
       opts->precision != IDF_TF32)
     return IDF_EINVAL;
   if (!(stack->blend_eps > 0) || !(stack->blend_eps <= 1)) return IDF_EINVAL;
@@ -828,6 +827,9 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
     std::string m = check_level(d, i);
     if (!m.empty()) return IDF_EINVAL;
     if (i == 1 && stack->n_levels == 2 && d.scale_to_parent <= 0 && stack->laplacian) return IDF_EINVAL;
+    // FP8 E4M3 contractions exist for the 16-channel networks only
+    if (opts->precision == IDF_FP8_E4M3 && d.test_denoiser == 0 && !small_net_eligible(unet_desc(d)))
+      return IDF_EUNSUPPORTED;
   }
   if (cudaSetDevice(opts->device) != cudaSuccess) {
     cudaGetLastError();
@@ -932,7 +934,7 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
         return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
       }
       unet_set_prof(L.unet, &W->prof);
-      unet_set_options(L.unet, opts->groupnorm_separate == 0, (long long)opts->device_wait_budget_cycles);
+      unet_set_options(L.unet, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles);
     }
   }
   if (stack->laplacian) {

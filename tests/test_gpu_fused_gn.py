@@ -1,4 +1,5 @@
-"""GroupNorm + SiLU inside the TF32 tensor-core convolutions' operand path.
+"""GroupNorm + SiLU inside the TF32 tensor-core convolutions' operand path
+(the option groupnorm_in_conv; off by default because it measured slower).
 
 The fused path applies, in shared memory, the same arithmetic as the
 separate GroupNorm apply pass ((x - mean) * rstd, SiLU with the fast
@@ -38,8 +39,8 @@ def test_unet_fused_equals_separate(idf, li):
     x = synth.window_batch(n, lv["in_ch"], lv["window"], seed=11 + li)
     xd = torch.from_numpy(x).cuda()
     outs = []
-    for sep in (False, True):
-        W = idf.World(0, st, wts, precision="tf32", max_batch=3, groupnorm_separate=sep)
+    for fused in (True, False):
+        W = idf.World(0, st, wts, precision="tf32", max_batch=3, groupnorm_in_conv=fused)
         yd = torch.empty((n, 1, lv["window"], lv["window"]), device="cuda")
         W.unet_forward(li, xd.data_ptr(), n, yd.data_ptr())
         torch.cuda.synchronize()
@@ -54,8 +55,8 @@ def test_query_fused_equals_separate(idf):
     wts = _weights(st)
     rect = (-70, 33, 96, 80)
     res = []
-    for sep in (False, True):
-        W = idf.World(0, st, wts, precision="tf32", groupnorm_separate=sep)
+    for fused in (True, False):
+        W = idf.World(0, st, wts, precision="tf32", groupnorm_in_conv=fused)
         res.append((W.query(*rect), W.query(*rect, kind=idf.IDF_OUT_METRES)))
         W.close()
     assert np.array_equal(res[0][0], res[1][0])

@@ -205,3 +205,75 @@ def test_eager_world_with_pool_equals_lazy_world():
     # the pooled F equals the serial one up to BLAS summation order
     e2 = S.EagerWorld(3, st, wts, y0, x0, h, w)
     assert np.max(np.abs(e2.model(y0, x0, h, w) - m_e)) <= 1e-13 * np.max(np.abs(m_e))
+
+
+# ----------------------------------------------------------- T variants (rounds)
+
+def _rounds(st, rounds):
+    st = synth.with_steps(st, sum(rounds))
+    st["level"][0]["round_steps"] = tuple(rounds)
+    return st
+
+
+@pytest.mark.parametrize("td", [1, 2])
+def test_rounds_equal_per_step_for_pixel_local_denoisers(td):
+    # with F independent of the window (constant, or the pixel's own value),
+    # every covering window follows the same pixel trajectory, so blending
+    # only at round ends changes nothing
+    base = synth.config1_stack(test_denoiser=td)
+    a = S.World(2, _rounds(base, (1, 1, 1, 1)), None).model(-9, 30, 21, 18)
+    for rs in ((2, 2), (4,), (1, 3)):
+        b = S.World(2, _rounds(base, rs), None).model(-9, 30, 21, 18)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("rounds", [(2, 2), (3, 1)])
+def test_rounds_local_coordinate_closed_form(rounds):
+    # F = c_in x + u/H - 2 v/H (window-local coordinates u, v): each window
+    # runs its own trajectory through a round, then the windows are blended;
+    # written out per pixel and per covering window
+    st = _rounds(synth.config1_stack(test_denoiser=3), rounds)
+    lv = st["level"][0]
+    H, s, K_ = lv["window"], lv["stride"], lv["steps"]
+    y0, x0, h, w = -23, 40, 19, 21
+    got = S.World(5, st, None).model(y0, x0, h, w)
+    sig = Sc.sigmas(K_, lv["sigma_max"], lv["sigma_min"], lv["rho"])
+    w1 = Sc.weight_1d(H, 1e-3)
+    Y = np.arange(y0, y0 + h)[:, None] + np.zeros((1, w), dtype=np.int64)
+    X = np.arange(x0, x0 + w)[None, :] + np.zeros((h, 1), dtype=np.int64)
+    noise = [N.normal_region(5, 0, j, x0, y0, w, h).astype(np.float64) for j in range(K_)]
+    J = sig[0] * noise[0]
+    j0 = 0
+    for m in rounds:
+        num = np.zeros((h, w))
+        den = np.zeros((h, w))
+        for di in (0, 1):
+            for dj in (0, 1):
+                u = Y - (Y // s - di) * s
+                v = X - (X // s - dj) * s
+                ww = w1[u] * w1[v]
+                g = u / H - 2.0 * v / H
+                x = J.copy()
+                for j in range(j0, j0 + m):
+                    cs, co, ci = Sc.edm_coeffs(sig[j], lv["sigma_data"])
+                    x = cs * x + co * (ci * x + g)
+                    if j + 1 < K_:
+                        x = x + sig[j + 1] * noise[j + 1]
+                num += ww * x
+                den += ww
+        J = num / den
+        j0 += m
+    assert np.max(np.abs(got - J)) < 1e-12 * np.max(np.abs(J))
+
+
+def test_rounds_lazy_equals_eager_and_cone_counts():
+    st = _rounds(synth.config1_stack(), (2, 2))
+    wts = _weights(st)
+    lz = S.World(0, st, wts)
+    lazy = lz.model(0, 0, 32, 32)
+    eager = S.eager_world_model(0, st, wts, 0, 0, 32, 32)
+    assert np.max(np.abs(lazy - eager)) <= 1e-12 * np.max(np.abs(eager))
+    # two rounds: the cone of a 2-step sampler, each window run for 2 steps
+    counts = K.cone_window_counts(0, 0, 32, 32, 32, 16, 2)
+    assert counts == [(2 + 1) ** 2, (2 + 3) ** 2]
+    assert lz.levels[0].phi_calls == 2 * sum(counts)
