@@ -101,6 +101,16 @@ typedef struct {
   double sigma_max, sigma_min, rho, sigma_data;
   int32_t scale_to_parent;   /* 0 for the first level; 8 for fine-under-coarse */
   int32_t test_denoiser;     /* 0 = UNet */
+  /* Blending at selected noise levels only (the T variants, Sec. 4
+   * "Latency", App. G): n_rounds > 0 groups the `steps` sampler steps into
+   * n_rounds rounds of round_steps[r] >= 1 steps (summing to steps).  Inside
+   * a round each window runs its steps on its own, x <- D(x; sigma_j) +
+   * sigma_{j+1} N(.) with the noise of absolute coordinates, and Eq. 2
+   * blends the windows only at the round's end; the dependency cone and the
+   * tile cache advance by rounds.  n_rounds = 0 (round_steps NULL): every
+   * step is blended.  round_steps is host memory, copied. */
+  const int32_t* round_steps;
+  int32_t n_rounds;
 } idf_level_desc;
 
 /*
@@ -194,7 +204,22 @@ idf_status idf_world_query_device(idf_world* world, int64_t x0, int64_t y0, int3
 idf_status idf_world_query_batch(idf_world* world, const idf_region* regions, int32_t n,
                                  idf_output_kind kind, void* cuda_stream);
 
-/* Drop every cached tile (Sec. 3.3: eviction makes windows unprocessed). */
+/* Persistent tile store ("Caching and Persistence", infinite-tensor
+ * appendix): open a directory of chunk files holding finalized tiles of the
+ * last round of every level.  Planning then reads such tiles from the store
+ * instead of computing their dependency cones (Lemma 3: a tile depends only
+ * on the seed and its position), and, with writable != 0, every query writes
+ * the final tiles it computed (a synchronous device-to-host copy and file
+ * writes at the end of the query).  The directory's manifest ties it to one
+ * world (seed, stack, weights, precision); opening it from another world
+ * returns IDF_EINVAL, as does a missing directory without writable, or a
+ * second open.  Files are plain chunk files of 16 x 16 tiles. */
+idf_status idf_world_store_open(idf_world* world, const char* dir, int32_t writable);
+
+/* Close the store (pending writes are complete when queries return). */
+idf_status idf_world_store_close(idf_world* world);
+
+/* Drop every cached tile (Sec. 3.3: eviction makes windows unprocessed). *//* Drop every cached tile (Sec. 3.3: eviction makes windows unprocessed). */
 idf_status idf_world_cache_clear(idf_world* world);
 
 /* JSON object with counters: windows evaluated per level, tiles computed,

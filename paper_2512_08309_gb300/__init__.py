@@ -28,6 +28,7 @@ PRECISIONS = {"fp32": IDF_FP32, "bf16": IDF_BF16, "fp8": IDF_FP8_E4M3, "bf16x3":
 EXPORTS = [
     "idf_world_create", "idf_world_query", "idf_world_query_device", "idf_world_query_batch",
     "idf_world_cache_clear", "idf_world_stats", "idf_world_last_error", "idf_world_destroy",
+    "idf_world_store_open", "idf_world_store_close",
     "idf_debug_cone", "idf_debug_cache_keys", "idf_debug_set_status", "idf_noise_fill",
     "idf_model_param_count", "idf_model_param_shape",
     "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo", "idf_laplacian_decode_noalloc",
@@ -52,6 +53,7 @@ class idf_level_desc(C.Structure):
         ("sigma_max", C.c_double), ("sigma_min", C.c_double), ("rho", C.c_double),
         ("sigma_data", C.c_double),
         ("scale_to_parent", C.c_int32), ("test_denoiser", C.c_int32),
+        ("round_steps", C.POINTER(C.c_int32)), ("n_rounds", C.c_int32),
     ]
 
 
@@ -98,6 +100,8 @@ def lib():
         "idf_world_query_device": ([vp, i64, i64, i32, i32, i32, vp, i64, vp], i32),
         "idf_world_query_batch": ([vp, C.POINTER(idf_region), i32, i32, vp], i32),
         "idf_world_cache_clear": ([vp], i32),
+        "idf_world_store_open": ([vp, C.c_char_p, i32], i32),
+        "idf_world_store_close": ([vp], i32),
         "idf_world_stats": ([vp, C.c_char_p, C.c_size_t], i32),
         "idf_world_last_error": ([vp], C.c_char_p),
         "idf_world_destroy": ([vp], None),
@@ -157,6 +161,12 @@ def level_desc(lv: dict, weights=None, keep: Optional[_Keep] = None) -> idf_leve
     d.window, d.stride, d.offset, d.steps = lv["window"], lv["stride"], lv["offset"], lv["steps"]
     d.sigma_max, d.sigma_min, d.rho, d.sigma_data = lv["sigma_max"], lv["sigma_min"], lv["rho"], lv["sigma_data"]
     d.scale_to_parent, d.test_denoiser = lv["scale_to_parent"], lv["test_denoiser"]
+    rs = lv.get("round_steps")
+    if rs:
+        arr = (C.c_int32 * len(rs))(*[int(v) for v in rs])
+        keep.refs.append(arr)
+        d.round_steps = arr
+        d.n_rounds = len(rs)
     return d
 
 
@@ -278,6 +288,14 @@ class World:
             arr[i] = idf_region(x0, y0, w, h, p, pitch)
         _check(lib().idf_world_query_batch(self._h, arr, len(regions), kind, _stream_ptr(stream)),
                "idf_world_query_batch", self._h)
+
+    def store_open(self, path: str, writable: bool = True):
+        """idf_world_store_open: persistent tile store in directory `path`."""
+        _check(lib().idf_world_store_open(self._h, path.encode(), 1 if writable else 0), "idf_world_store_open",
+               self._h)
+
+    def store_close(self):
+        _check(lib().idf_world_store_close(self._h), "idf_world_store_close", self._h)
 
     def cache_clear(self):
         _check(lib().idf_world_cache_clear(self._h), "idf_world_cache_clear", self._h)

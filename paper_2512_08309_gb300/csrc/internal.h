@@ -45,8 +45,28 @@ struct GatherArgs {
   int cond_w, cond_h, cond_f;
   float* x_in;               // [n_win][H][H][in_ch] float32 (NHWC)
   int* err_flag;             // device flag set on out-of-range reads
+  float* xs = nullptr;       // optional [n_win][H][H]: the window state J_k[R_i] (multi-step rounds)
 };
 void launch_gather(const GatherArgs& a, cudaStream_t st);
+
+// One window-local sampler step inside a multi-step round (blending only at
+// selected noise levels): D = c_skip xs + c_out F per window pixel; with
+// last, F = D (the round's result, blended next); otherwise xs = D +
+// sigma_next N(seed, level, step_next, .) (absolute coordinates) and the
+// network input channel 0 becomes c_in_next xs.
+struct WindowStepArgs {
+  float* x_in;               // [n_win][H][H][in_ch]
+  float* xs;                 // [n_win][H][H]
+  float* F;                  // [n_win][H][H]
+  const int32_t* win_ij;     // [n_win][2]
+  int n_win, H, s, in_ch;
+  float c_skip, c_out, c_in_next, sigma_next;
+  int noise, last;
+  uint32_t step_next;
+  uint64_t seed;
+  uint32_t level;
+};
+void launch_window_step(const WindowStepArgs& a, cudaStream_t st);
 
 struct BlendArgs {
   const float* pool;
@@ -245,6 +265,16 @@ void small_net_destroy(SmallNet* s);
 // F (n, 32, 32) float32 of x (n, 32, 32, in_ch) NHWC float32
 bool small_net_forward(const SmallNet* s, const float* x, int n, float* F, int* status, long long wait_limit,
                        cudaStream_t st, std::string* err);
+
+// Persistent tile store (store.cpp): chunk files of finalized tiles in a
+// directory, tied to a world identity by a manifest.
+struct TileStore;
+TileStore* store_open(const std::string& dir, uint64_t identity, const std::vector<int>& tile_side, bool writable,
+                      std::string* err);
+void store_close(TileStore* s);
+bool store_has(TileStore* s, int level, int32_t ty, int32_t tx);
+bool store_read(TileStore* s, int level, int32_t ty, int32_t tx, float* dst);
+bool store_write(TileStore* s, int level, int32_t ty, int32_t tx, const float* src);
 
 // float32 building blocks (unet.cu), NHWC, square images
 void launch_conv_f32(const float* x, const float* wk, const float* res, float* y, int n, int H, int W,

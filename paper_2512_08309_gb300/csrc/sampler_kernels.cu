@@ -55,6 +55,7 @@ __global__ void gather_kernel(GatherArgs a) {
     }
     float* o = a.x_in + idx * a.in_ch;
     o[0] = __fmul_rn(a.c_in, J);
+    if (a.xs) a.xs[idx] = J;
     if (a.in_ch == 2) {
       const int64_t cy = fdiv(Y, a.cond_f) - a.cond_y0, cx = fdiv(X, a.cond_f) - a.cond_x0;
       float c = 0.0f;
@@ -71,6 +72,35 @@ __global__ void gather_kernel(GatherArgs a) {
 void launch_gather(const GatherArgs& a, cudaStream_t st) {
   const int64_t n = (int64_t)a.H * a.H * a.n_win;
   gather_kernel<<<grid_for(n, 256), 256, 0, st>>>(a);
+}
+
+// ------------------------------------------------------------ window step
+__global__ void window_step_kernel(WindowStepArgs a) {
+  const int H = a.H;
+  const int64_t per = (int64_t)H * H;
+  const int64_t n = per * a.n_win;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const float d = __fadd_rn(__fmul_rn(a.c_skip, a.xs[idx]), __fmul_rn(a.c_out, a.F[idx]));
+    if (a.last) {
+      a.F[idx] = d;
+      continue;
+    }
+    float xn = d;
+    if (a.noise) {
+      const int b = (int)(idx / per);
+      const int p = (int)(idx % per);
+      const int64_t Y = (int64_t)a.win_ij[2 * b] * a.s + p / H, X = (int64_t)a.win_ij[2 * b + 1] * a.s + p % H;
+      xn = __fadd_rn(d, __fmul_rn(a.sigma_next, normal_at(a.seed, a.level, a.step_next, X, Y)));
+    }
+    a.xs[idx] = xn;
+    a.x_in[idx * a.in_ch] = __fmul_rn(a.c_in_next, xn);
+  }
+}
+
+void launch_window_step(const WindowStepArgs& a, cudaStream_t st) {
+  const int64_t n = (int64_t)a.H * a.H * a.n_win;
+  window_step_kernel<<<grid_for(n, 256), 256, 0, st>>>(a);
 }
 
 // ------------------------------------------------------------------ blend

@@ -2398,7 +2398,7 @@ bool resblock_cat_half(Ctx& c, size_t& wi, const LevelBufs& lb, const LevelBufs&
     return true;
   }
   // statistics of the concat's groups from the block partials of a and b
-  const double wr = (double)sizeof(TA) * 2 * (sp ? 2 : 1);
+  const double wr = (double)sizeof(TA) * (std::is_same<TA, tf32>::value ? 1 : 2) * (sp ? 2 : 1);
   const double nb = (double)c.n * ((double)Hh * Hh * Ca + (double)H * H * Cb);
   const int pr = c.u->prof ? c.u->prof->begin(PK_GROUPNORM, c.st, 0.0, nb * (4.0 + wr)) : -1;
   const BlkSrc bsrc{bsa, bsb, Ca, Cb, Hh * Hh / 32, H * H / 32};

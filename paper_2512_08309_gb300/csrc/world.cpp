@@ -114,13 +114,19 @@ struct StepPlan {
 struct Level {
   idf_level_desc d{};
   std::vector<int32_t> ch;
-  int H = 0, s = 0, r = 0, K = 0, index = 0;
+  // K sampler steps grouped into R blended rounds of rsteps[k] steps from
+  // rstart[k] (one step per round unless the level asks otherwise); the
+  // cone, the cache and the tables are indexed by round
+  int H = 0, s = 0, r = 0, K = 0, R = 0, index = 0;
+  std::vector<int> rsteps, rstart;
+  std::vector<int32_t> rsteps_copy;
   std::vector<double> sig, c_skip, c_out, c_in;
   float* d_w1 = nullptr;
   float* d_invB1 = nullptr;
   UNet* unet = nullptr;
   TileCache cache;
   int64_t windows_evaluated = 0, tiles_computed = 0;
+  int64_t store_reads = 0, store_writes = 0;
 };
 
 }  // namespace
@@ -137,6 +143,7 @@ struct idf_world {
   // growable device buffers
   float* F = nullptr; size_t F_cap = 0;
   float* x_in = nullptr; size_t x_cap = 0;
+  float* xs = nullptr; size_t xs_cap = 0;          // window states of multi-step rounds
   int32_t* tab = nullptr; size_t tab_cap = 0;
   float* dense = nullptr; size_t dense_cap = 0;    // assembled level results
   float* dec = nullptr; size_t dec_cap = 0;        // decode scratch
@@ -148,6 +155,11 @@ struct idf_world {
   void* arena = nullptr; size_t arena_bytes = 0;  // UNet activations, shared by the levels
   int64_t launches = 0, queries = 0;
   Prof prof;
+  // persistent tile store (idf_world_store_open) and its pinned staging
+  uint64_t identity = 0;
+  TileStore* store = nullptr;
+  bool store_writable = false;
+  float* h_store = nullptr; size_t h_store_cap = 0;
 };
 
 namespace {
@@ -229,6 +241,15 @@ std::string check_level(const idf_level_desc& d, int index) {
   if (d.in_ch != (d.scale_to_parent > 0 ? 2 : 1)) return bad("in_ch must be 1, or 2 for a conditioned level");
   if (d.scale_to_parent > 0 && index == 0) return bad("the first level has no parent");
   if (d.test_denoiser < 0 || d.test_denoiser > 3) return bad("test_denoiser must be 0..3");
+  if (d.n_rounds < 0 || (d.n_rounds > 0 && !d.round_steps)) return bad("round_steps missing");
+  if (d.n_rounds > 0) {
+    int64_t sum = 0;
+    for (int r = 0; r < d.n_rounds; ++r) {
+      if (d.round_steps[r] < 1) return bad("round_steps must be >= 1");
+      sum += d.round_steps[r];
+    }
+    if (sum != d.steps) return bad("round_steps must sum to steps");
+  }
   if (d.test_denoiser == 0) {
     if (d.levels < 1 || d.levels > 6 || !d.channels) return bad("levels must be in [1, 6] with channels");
     if (d.window % (1 << (d.levels - 1))) return bad("window must be divisible by 2^(levels-1)");
@@ -251,6 +272,10 @@ struct LevelPlan {
   int64_t wi_min = 0, wi_max = -1, wj_min = 0, wj_max = -1;
   bool any_windows = false;
   size_t n_win_max = 0;
+  // final-round tiles read from the persistent store instead of computed:
+  // (slot, key) once slots are allocated
+  std::vector<uint64_t> from_store;
+  std::vector<std::pair<int32_t, uint64_t>> loads;
 };
 
 struct RectT {
@@ -258,10 +283,12 @@ struct RectT {
 };
 
 // Plan (and, unless dry, allocate cache slots for) the query of J_K over the
-// tile rects.  Returns false with a message on cache exhaustion.
+// tile rects.  With a persistent store, final-round tiles it holds count as
+// available (read into cache slots instead of computed).  Returns false with
+// a message on cache exhaustion.
 bool plan_level(Level& L, const std::vector<RectT>& rects, bool dry, LevelPlan& P,
-                std::string* err) {
-  const int K = L.K, r = L.r;
+                std::string* err, TileStore* store = nullptr) {
+  const int K = L.R, r = L.r;
   TileCache& C = L.cache;
   P.steps.assign(K, StepPlan());
   std::vector<uint64_t> need;
@@ -285,6 +312,8 @@ bool plan_level(Level& L, const std::vector<RectT>& rects, bool dry, LevelPlan& 
           C.touch(it->second);
           C.hits++;
         }
+      } else if (k == K && store && store_has(store, L.index, khi(t), klo(t))) {
+        P.from_store.push_back(t);
       } else {
         mk.push_back(t);
       }
@@ -328,8 +357,10 @@ bool plan_level(Level& L, const std::vector<RectT>& rects, bool dry, LevelPlan& 
   // allocate slots for the missing tiles, step by step; on exhaustion undo
   // every insertion of this plan so that no uncomputed tile stays visible
   std::vector<std::pair<int, uint64_t>> inserted;
-  for (int k = 1; k <= K; ++k) {
+  for (uint64_t t : P.from_store) missing[0].push_back(t);  // (slots first; J_0 is never cached)
+  for (int k = 0; k <= K; ++k) {
     for (uint64_t t : missing[k]) {
+      const int kk = k == 0 ? K : k;
       const int32_t sl = C.alloc();
       if (sl < 0) {
         for (auto& kt : inserted) {
@@ -340,12 +371,15 @@ bool plan_level(Level& L, const std::vector<RectT>& rects, bool dry, LevelPlan& 
           C.free_list.push_back(os);
         }
         *err = "tile cache too small for this query's working set; raise cache_bytes";
+        P.loads.clear();
         return false;
       }
-      C.insert(k, t, sl);
-      inserted.emplace_back(k, t);
+      C.insert(kk, t, sl);
+      inserted.emplace_back(kk, t);
+      if (k == 0) P.loads.emplace_back(sl, t);
     }
   }
+  missing[0].clear();
   // tables
   for (int k = 0; k < K; ++k) {
     StepPlan& sp = P.steps[k];
@@ -403,7 +437,7 @@ struct Dense {
 };
 
 bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
-  const int K = L.K, r = L.r, H = L.H, s = L.s;
+  const int K = L.R, r = L.r, H = L.H, s = L.s;
   cudaStream_t st = W->st;
   // upload every table in one copy
   size_t total = 0;
@@ -419,6 +453,8 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
     // the previous copy from the staging buffer must be done before it is reused
     if (!cuda_ok(W, cudaStreamSynchronize(st), "sync")) return false;
     if (W->h_tab) cudaFreeHost(W->h_tab);
+  if (W->h_store) cudaFreeHost(W->h_store);
+  store_close(W->store);
     W->h_tab = nullptr;
     W->h_tab_cap = 0;
     if (cudaMallocHost((void**)&W->h_tab, total * 4 * 3 / 2) != cudaSuccess) {
@@ -441,10 +477,16 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
   const int B = L.unet ? unet_max_batch(L.unet) : 4096;
   if (!grow(W, &W->F, &W->F_cap, P.n_win_max * (size_t)H * H, "window outputs")) return false;
   if (!grow(W, &W->x_in, &W->x_cap, (size_t)std::min<size_t>(B, P.n_win_max) * H * H * L.d.in_ch, "window inputs")) return false;
+  bool multi = false;
+  for (int m : L.rsteps) multi = multi || m > 1;
+  if (multi && !grow(W, &W->xs, &W->xs_cap, (size_t)std::min<size_t>(B, P.n_win_max) * H * H, "window states"))
+    return false;
   for (int k = 0; k < K; ++k) {
     StepPlan& sp = P.steps[k];
     const int nw = (int)(sp.win_ij.size() / 2);
     if (nw == 0) continue;
+    // round k: sampler steps j0 .. jl, window-local between its blends
+    const int j0 = L.rstart[k], m = L.rsteps[k], jl = j0 + m - 1;
     for (int b0 = 0; b0 < nw; b0 += B) {
       const int nb = std::min(B, nw - b0);
       GatherArgs g{};
@@ -453,8 +495,9 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
       g.win_ij = W->tab + sp.off_win_ij + 2 * (size_t)b0;
       g.n_win = nb;
       g.H = H; g.s = s; g.r = r; g.in_ch = L.d.in_ch;
-      g.c_in = (float)L.c_in[k];
+      g.c_in = (float)L.c_in[j0];
       g.sigma0 = (float)L.sig[0];
+      g.xs = m > 1 ? W->xs : nullptr;
       g.noise_step0 = k == 0;
       g.seed = W->seed;
       g.level = (uint32_t)L.index;
@@ -469,23 +512,49 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
       W->prof.end(pr, st);
       W->launches++;
       float* Fb = W->F + (size_t)b0 * H * H;
-      if (L.d.test_denoiser) {
-        pr = W->prof.begin(PK_DENOISE_TEST, st, 0.0, (double)nb * H * H * 4 * (L.d.in_ch + 1));
-        launch_test_denoiser(L.d.test_denoiser, W->x_in, nb, H, L.d.in_ch, Fb, st);
-        W->prof.end(pr, st);
-        W->launches++;
-      } else {
-        Err e;
-        const int64_t l0 = unet_launches(L.unet);
-        if (!unet_forward(L.unet, W->x_in, nb, Fb, st, &e)) {
-          W->last_error = e.msg;
-          W->poisoned = e.code == 3;
-          return false;
+      for (int i = 0; i < m; ++i) {
+        const int j = j0 + i;
+        if (L.d.test_denoiser) {
+          pr = W->prof.begin(PK_DENOISE_TEST, st, 0.0, (double)nb * H * H * 4 * (L.d.in_ch + 1));
+          launch_test_denoiser(L.d.test_denoiser, W->x_in, nb, H, L.d.in_ch, Fb, st);
+          W->prof.end(pr, st);
+          W->launches++;
+        } else {
+          Err e;
+          const int64_t l0 = unet_launches(L.unet);
+          if (!unet_forward(L.unet, W->x_in, nb, Fb, st, &e)) {
+            W->last_error = e.msg;
+            W->poisoned = e.code == 3;
+            return false;
+          }
+          W->launches += unet_launches(L.unet) - l0;
         }
-        W->launches += unet_launches(L.unet) - l0;
+        if (m > 1) {
+          // window-local update; the round's last step leaves D in F
+          WindowStepArgs ws{};
+          ws.x_in = W->x_in;
+          ws.xs = W->xs;
+          ws.F = Fb;
+          ws.win_ij = g.win_ij;
+          ws.n_win = nb;
+          ws.H = H; ws.s = s; ws.in_ch = L.d.in_ch;
+          ws.c_skip = (float)L.c_skip[j];
+          ws.c_out = (float)L.c_out[j];
+          ws.last = i == m - 1;
+          ws.c_in_next = ws.last ? 0.0f : (float)L.c_in[j + 1];
+          ws.noise = !ws.last && j + 1 < L.K;
+          ws.sigma_next = j + 1 < L.K ? (float)L.sig[j + 1] : 0.0f;
+          ws.step_next = (uint32_t)(j + 1);
+          ws.seed = W->seed;
+          ws.level = (uint32_t)L.index;
+          pr = W->prof.begin(PK_GATHER, st, 0.0, (double)nb * H * H * 4 * (ws.last ? 3 : 4 + L.d.in_ch));
+          launch_window_step(ws, st);
+          W->prof.end(pr, st);
+          W->launches++;
+        }
       }
     }
-    L.windows_evaluated += nw;
+    L.windows_evaluated += (int64_t)nw * m;
     BlendArgs bl{};
     bl.pool = L.cache.pool;
     bl.pool_out = L.cache.pool;
@@ -496,21 +565,23 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
     bl.invB1 = L.d_invB1;
     bl.n_tiles = (int)(sp.tiles.size() / 4);
     bl.H = H; bl.s = s; bl.r = r;
-    bl.c_skip = (float)L.c_skip[k];
-    bl.c_out = (float)L.c_out[k];
-    bl.c_in = (float)L.c_in[k];
+    // one step: J = c_skip J_k + c_out (blended F) + noise; several steps:
+    // F already holds each window's D, J = (blended D) + noise
+    bl.c_skip = m == 1 ? (float)L.c_skip[j0] : 0.0f;
+    bl.c_out = m == 1 ? (float)L.c_out[j0] : 1.0f;
+    bl.c_in = (float)L.c_in[j0];
     bl.sigma0 = (float)L.sig[0];
     bl.noise_in = k == 0;
-    bl.noise_next = k + 1 < K;
-    bl.sigma_next = k + 1 < K ? (float)L.sig[k + 1] : 0.0f;
-    bl.step_next = (uint32_t)(k + 1);
+    bl.noise_next = jl + 1 < L.K;
+    bl.sigma_next = jl + 1 < L.K ? (float)L.sig[jl + 1] : 0.0f;
+    bl.step_next = (uint32_t)(jl + 1);
     bl.seed = W->seed;
     bl.level = (uint32_t)L.index;
     // algorithmic bytes per tile pixel: r^2 window outputs, J_k (unless it is
     // the noise) and J_{k+1}; the work field counts the normal samples drawn
     // (J_0 at the first step, the re-noise before every later one), whose
     // Philox + Box-Muller arithmetic, not memory, bounds this kernel
-    const double normals = (double)bl.n_tiles * s * s * ((k == 0 ? 1 : 0) + (k + 1 < K ? 1 : 0));
+    const double normals = (double)bl.n_tiles * s * s * ((k == 0 ? 1 : 0) + (jl + 1 < L.K ? 1 : 0));
     const int pr = W->prof.begin(PK_BLEND, st, normals, (double)bl.n_tiles * s * s * 4.0 * (r * r + (k ? 2 : 1)));
     launch_blend(bl, st);
     W->prof.end(pr, st);
@@ -528,8 +599,8 @@ bool assemble(idf_world* W, Level& L, int64_t x0, int64_t y0, int w, int h, floa
   std::vector<int32_t> slots((size_t)nty * ntx);
   for (int a = 0; a < nty; ++a)
     for (int b = 0; b < ntx; ++b) {
-      auto it = L.cache.map[L.K].find(tkey((int32_t)(R.ty0 + a), (int32_t)(R.tx0 + b)));
-      if (it == L.cache.map[L.K].end()) {
+      auto it = L.cache.map[L.R].find(tkey((int32_t)(R.ty0 + a), (int32_t)(R.tx0 + b)));
+      if (it == L.cache.map[L.R].end()) {
         W->last_error = "internal: final tile missing";
         return false;
       }
@@ -552,6 +623,64 @@ bool assemble(idf_world* W, Level& L, int64_t x0, int64_t y0, int w, int h, floa
   // may go out of scope now
   cudaFreeAsync(d_slots, W->st);
   return cuda_ok(W, cudaGetLastError(), "assemble");
+}
+
+// pinned staging of n floats for store transfers (waits for earlier copies)
+bool store_staging(idf_world* W, size_t n) {
+  if (!cuda_ok(W, cudaStreamSynchronize(W->st), "sync")) return false;
+  if (n <= W->h_store_cap) return true;
+  if (W->h_store) cudaFreeHost(W->h_store);
+  W->h_store = nullptr;
+  W->h_store_cap = 0;
+  if (cudaMallocHost((void**)&W->h_store, n * 4) != cudaSuccess) {
+    cudaGetLastError();
+    W->last_error = "cudaMallocHost store staging failed";
+    return false;
+  }
+  W->h_store_cap = n;
+  return true;
+}
+
+// read the plan's stored final tiles into their cache slots
+bool store_load(idf_world* W, Level& L, const LevelPlan& P) {
+  if (P.loads.empty()) return true;
+  const size_t ts = (size_t)L.s * L.s;
+  if (!store_staging(W, P.loads.size() * ts)) return false;
+  for (size_t i = 0; i < P.loads.size(); ++i) {
+    const uint64_t t = P.loads[i].second;
+    if (!store_read(W->store, L.index, khi(t), klo(t), W->h_store + i * ts)) {
+      W->last_error = "tile store read failed";
+      return false;
+    }
+    if (!cuda_ok(W, cudaMemcpyAsync(L.cache.pool + (size_t)P.loads[i].first * ts, W->h_store + i * ts, ts * 4,
+                                    cudaMemcpyHostToDevice, W->st),
+                 "store upload"))
+      return false;
+  }
+  L.store_reads += (int64_t)P.loads.size();
+  return true;
+}
+
+// write the final-round tiles this plan computed into the store
+bool store_save(idf_world* W, Level& L, const LevelPlan& P) {
+  if (P.steps.empty()) return true;
+  const StepPlan& sp = P.steps[L.R - 1];
+  const size_t nt = sp.tiles.size() / 4, ts = (size_t)L.s * L.s;
+  if (nt == 0) return true;
+  if (!store_staging(W, nt * ts)) return false;
+  for (size_t t = 0; t < nt; ++t)
+    if (!cuda_ok(W, cudaMemcpyAsync(W->h_store + t * ts, L.cache.pool + (size_t)sp.tiles[4 * t + 3] * ts, ts * 4,
+                                    cudaMemcpyDeviceToHost, W->st),
+                 "store download"))
+      return false;
+  if (!cuda_ok(W, cudaStreamSynchronize(W->st), "sync")) return false;
+  for (size_t t = 0; t < nt; ++t)
+    if (!store_write(W->store, L.index, sp.tiles[4 * t], sp.tiles[4 * t + 1], W->h_store + t * ts)) {
+      W->last_error = "tile store write failed";
+      return false;
+    }
+  L.store_writes += (int64_t)nt;
+  return true;
 }
 
 // Decode halo: coarse rect of l^ read by the final upsampling, and the
@@ -601,7 +730,7 @@ bool valid_region(int64_t x0, int64_t y0, int64_t w, int64_t h) {
 }
 
 bool tiles_fit(const Level& L, int64_t x0, int64_t y0, int64_t w, int64_t h) {
-  const int64_t margin = (int64_t)(L.K + 2) * L.r + 2;
+  const int64_t margin = (int64_t)(L.R + 2) * L.r + 2;
   auto fits = [&](int64_t v) { return v > INT32_MIN + margin && v < INT32_MAX - margin; };
   return fits(fdiv(x0, L.s)) && fits(fdiv(y0, L.s)) && fits(fdiv(x0 + w - 1, L.s)) &&
          fits(fdiv(y0 + h - 1, L.s));
@@ -642,7 +771,9 @@ idf_status serve(idf_world* W, const std::vector<Req>& reqs, idf_output_kind kin
   }
   std::string err;
   LevelPlan fp;
-  if (!plan_level(F, frects, false, fp, &err)) return fail(W, IDF_ENOMEM, err);
+  if (!plan_level(F, frects, false, fp, &err, W->store)) return fail(W, IDF_ENOMEM, err);
+  if (!store_load(W, F, fp)) return fail(W, W->poisoned ? IDF_ECUDA : IDF_EINTERNAL, W->last_error);
+  LevelPlan cp;
   Dense cond;
   std::vector<Dense> lows(reqs.size());
   if (nl == 2) {
@@ -663,8 +794,8 @@ idf_status serve(idf_world* W, const std::vector<Req>& reqs, idf_output_kind kin
     if (kind == IDF_OUT_METRES)
       for (auto& hl : halos) crects.push_back(tile_rect(C, hl.Lx0, hl.Ly0, hl.Lw, hl.Lh));
     if (!crects.empty()) {
-      LevelPlan cp;
-      if (!plan_level(C, crects, false, cp, &err)) return fail(W, IDF_ENOMEM, err);
+      if (!plan_level(C, crects, false, cp, &err, W->store)) return fail(W, IDF_ENOMEM, err);
+      if (!store_load(W, C, cp)) return fail(W, W->poisoned ? IDF_ECUDA : IDF_EINTERNAL, W->last_error);
       if (!run_level(W, C, cp, nullptr)) return fail(W, W->poisoned ? IDF_ECUDA : IDF_ENOMEM, W->last_error);
     }
     // dense coarse results: one for the conditioning, one per decode
@@ -740,6 +871,10 @@ idf_status serve(idf_world* W, const std::vector<Req>& reqs, idf_output_kind kin
     W->launches += 4;
   }
   if (!cuda_ok(W, cudaGetLastError(), "decode launch")) return fail(W, IDF_ECUDA, W->last_error);
+  if (W->store && W->store_writable) {
+    if (nl == 2 && !store_save(W, W->lv[0], cp)) return fail(W, W->poisoned ? IDF_ECUDA : IDF_EINTERNAL, W->last_error);
+    if (!store_save(W, F, fp)) return fail(W, W->poisoned ? IDF_ECUDA : IDF_EINTERNAL, W->last_error);
+  }
   W->queries += (int64_t)reqs.size();
   return IDF_OK;
 }
@@ -868,6 +1003,36 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
     batches[i] = mb;
     arena_need = std::max(arena_need, unet_arena_bytes(ud, opts->precision, mb));
   }
+  // world identity for the persistent tile store: FNV-1a over the seed, the
+  // precision, the stack and level descriptions and the weights
+  {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+      const uint8_t* b = (const uint8_t*)p;
+      for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    mix(&seed, sizeof seed);
+    mix(&opts->precision, sizeof opts->precision);
+    const double sd[7] = {stack->lap_blur_sigma, stack->low_mu, stack->low_scale, stack->res_scale, stack->blend_eps,
+                          (double)stack->lap_factor, (double)stack->lap_radius};
+    mix(sd, sizeof sd);
+    mix(&stack->laplacian, sizeof stack->laplacian);
+    if (stack->low_band_fixture)
+      mix(stack->low_band_fixture, (size_t)stack->fixture_period * stack->fixture_period * sizeof(float));
+    for (int i = 0; i < stack->n_levels; ++i) {
+      const idf_level_desc& d = stack->level[i];
+      const int32_t iv[13] = {d.levels, d.in_ch, d.out_ch, d.gn_groups, d.attn_at_bottom, d.attn_heads,
+                              d.window, d.stride, d.offset, d.steps, d.scale_to_parent, d.test_denoiser,
+                              d.n_rounds};
+      mix(iv, sizeof iv);
+      if (d.channels && d.test_denoiser == 0) mix(d.channels, (size_t)d.levels * sizeof(int32_t));
+      if (d.round_steps && d.n_rounds > 0) mix(d.round_steps, (size_t)d.n_rounds * sizeof(int32_t));
+      const double dv[4] = {d.sigma_max, d.sigma_min, d.rho, d.sigma_data};
+      mix(dv, sizeof dv);
+      if (d.weights && d.test_denoiser == 0) mix(d.weights, d.n_weights * sizeof(float));
+    }
+    W->identity = h;
+  }
   W->prof.on = opts->profile != 0;
   W->lv.resize(stack->n_levels);
   for (int i = 0; i < stack->n_levels; ++i) {
@@ -883,6 +1048,16 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
     L.s = L.d.stride;
     L.r = L.d.window / L.d.stride;
     L.K = L.d.steps;
+    if (L.d.n_rounds > 0) {
+      L.rsteps.assign(L.d.round_steps, L.d.round_steps + L.d.n_rounds);
+    } else {
+      L.rsteps.assign(L.K, 1);
+    }
+    L.R = (int)L.rsteps.size();
+    L.rstart.resize(L.R);
+    for (int k = 0, j = 0; k < L.R; j += L.rsteps[k], ++k) L.rstart[k] = j;
+    L.rsteps_copy.assign(L.rsteps.begin(), L.rsteps.end());
+    L.d.round_steps = L.rsteps_copy.data();
     schedule(L);
     // blend tables: w1(u) = 1 - (1-eps) |u - c| / c, c = (H-1)/2; B1(a) = sum_m w1(a + m s)
     std::vector<float> w1(L.H), ib(L.s);
@@ -909,7 +1084,7 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
     if (cudaMalloc(&C.pool, (size_t)C.n_slots * L.s * L.s * 4) != cudaSuccess) {
       return bail(IDF_ENOMEM);
     }
-    C.map.resize(L.K + 1);
+    C.map.resize(L.R + 1);
     C.slot_step.assign(C.n_slots, 0);
     C.slot_key.assign(C.n_slots, 0);
     C.prv.assign(C.n_slots, -1);
@@ -962,9 +1137,11 @@ void idf_world_destroy(idf_world* W) {
     cudaFree(L.d_invB1);
     cudaFree(L.cache.pool);
   }
-  cudaFree(W->F); cudaFree(W->x_in); cudaFree(W->tab); cudaFree(W->dense); cudaFree(W->dec);
+  cudaFree(W->F); cudaFree(W->x_in); cudaFree(W->xs); cudaFree(W->tab); cudaFree(W->dense); cudaFree(W->dec);
   cudaFree(W->outbuf); cudaFree(W->d_taps); cudaFree(W->d_fixture); cudaFree(W->d_err); cudaFree(W->arena);
   if (W->h_tab) cudaFreeHost(W->h_tab);
+  if (W->h_store) cudaFreeHost(W->h_store);
+  store_close(W->store);
   if (W->ev_join) cudaEventDestroy(W->ev_join);
   if (W->st) cudaStreamDestroy(W->st);
   delete W;
@@ -1051,10 +1228,11 @@ idf_status idf_world_stats(const idf_world* Wc, char* buf, size_t len) {
     snprintf(b, sizeof b,
              "%s{\"windows_evaluated\": %lld, \"tiles_computed\": %lld, \"cache_hits\": %lld, "
              "\"cache_misses\": %lld, \"evictions\": %lld, \"tiles_cached\": %zu, \"slots\": %lld, "
-             "\"unet_batch\": %d}",
+             "\"unet_batch\": %d, \"store_reads\": %lld, \"store_writes\": %lld}",
              i ? ", " : "", (long long)L.windows_evaluated, (long long)L.tiles_computed,
              (long long)L.cache.hits, (long long)L.cache.misses, (long long)L.cache.evictions, used,
-             (long long)L.cache.n_slots, L.unet ? unet_max_batch(L.unet) : 0);
+             (long long)L.cache.n_slots, L.unet ? unet_max_batch(L.unet) : 0, (long long)L.store_reads,
+             (long long)L.store_writes);
     s += b;
   }
   char b[128];
@@ -1082,12 +1260,12 @@ idf_status idf_debug_cone(idf_world* W, int64_t x0, int64_t y0, int32_t w, int32
   if (!W || !n_out) return IDF_EINVAL;
   if (level < 0 || level >= (int)W->lv.size()) return fail(W, IDF_EINVAL, "bad level");
   Level& L = W->lv[level];
-  if (step < 0 || step >= L.K) return fail(W, IDF_EINVAL, "bad step");
+  if (step < 0 || step >= L.R) return fail(W, IDF_EINVAL, "bad step");
   if (!valid_region(x0, y0, w, h) || !tiles_fit(L, x0, y0, w, h)) return fail(W, IDF_EINVAL, "invalid region");
   LevelPlan P;
   std::string err;
   std::vector<RectT> rs{tile_rect(L, x0, y0, w, h)};
-  plan_level(L, rs, true, P, &err);
+  plan_level(L, rs, true, P, &err, W->store);
   const auto& wi = P.steps[step].win_ij;
   const int32_t n = (int32_t)(wi.size() / 2);
   *n_out = n;
@@ -1099,12 +1277,34 @@ idf_status idf_debug_cone(idf_world* W, int64_t x0, int64_t y0, int32_t w, int32
   return IDF_OK;
 }
 
+idf_status idf_world_store_open(idf_world* W, const char* dir, int32_t writable) {
+  if (!W || !dir || !dir[0]) return IDF_EINVAL;
+  if (W->store) return fail(W, IDF_EINVAL, "a tile store is already open on this world");
+  std::vector<int> side;
+  for (auto& L : W->lv) side.push_back(L.s);
+  std::string err;
+  TileStore* s = store_open(dir, W->identity, side, writable != 0, &err);
+  if (!s) return fail(W, IDF_EINVAL, err);
+  W->store = s;
+  W->store_writable = writable != 0;
+  return IDF_OK;
+}
+
+idf_status idf_world_store_close(idf_world* W) {
+  if (!W) return IDF_EINVAL;
+  if (!cuda_ok(W, cudaStreamSynchronize(W->st), "sync")) return IDF_ECUDA;
+  store_close(W->store);
+  W->store = nullptr;
+  W->store_writable = false;
+  return IDF_OK;
+}
+
 idf_status idf_debug_cache_keys(idf_world* W, int32_t level, int32_t step, int32_t* ty_tx, int32_t cap,
                                 int32_t* n_out) {
   if (!W || !n_out) return IDF_EINVAL;
   if (level < 0 || level >= (int)W->lv.size()) return fail(W, IDF_EINVAL, "bad level");
   Level& L = W->lv[level];
-  if (step < 1 || step > L.K) return fail(W, IDF_EINVAL, "bad step");
+  if (step < 1 || step > L.R) return fail(W, IDF_EINVAL, "bad step");
   std::vector<uint64_t> keys;
   keys.reserve(L.cache.map[step].size());
   for (auto& kv : L.cache.map[step]) keys.push_back(kv.first);

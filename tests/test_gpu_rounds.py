@@ -1,0 +1,106 @@
+"""Blending only at selected noise levels (the T variants): a level's K
+sampler steps grouped into rounds, each window running a round's steps on
+its own and Eq. 2 blending the windows at the round's end.  Checked against
+the FP64 oracle's literal per-window rounds: the 16-channel UNet (FP32 and
+the fused BF16 kernel), the local-coordinate test denoiser (whose per-window
+trajectories differ, so a wrong round grouping shows), a two-level stack,
+and the windows evaluated per round (the cone advances by rounds)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import kappa as OK
+from oracle import sampler as OS
+from oracle import unet as OU
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def idf():
+    import paper_2512_08309_gb300 as m
+    m.lib()
+    return m
+
+
+def _rounds(st, rounds, levels=None):
+    st = synth.with_steps(st, sum(rounds))
+    for i, lv in enumerate(st["level"]):
+        if levels is None or i in levels:
+            lv["round_steps"] = tuple(rounds)
+    return st
+
+
+def _weights(st):
+    return [synth.weights([s for _, s in OU.param_shapes(lv)], 0, i) for i, lv in enumerate(st["level"])]
+
+
+@pytest.mark.parametrize("rounds", [(2, 2), (4,), (1, 3)])
+def test_rounds_fp32_unet_against_oracle(idf, rounds):
+    st = _rounds(synth.config1_stack(), rounds)
+    wts = _weights(st)
+    rect = (-20, 9, 48, 40)
+    ref = OS.World(0, st, wts).model(rect[1], rect[0], rect[3], rect[2])
+    W = idf.World(0, st, wts, precision="fp32")
+    got = W.query(*rect).astype(np.float64)
+    W.close()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * ref.std()
+
+
+def test_rounds_bf16_fused_kernel_against_oracle(idf):
+    st = _rounds(synth.config1_stack(), (2, 2))
+    wts = _weights(st)
+    rect = (0, 0, 64, 64)
+    ref = OS.World(0, st, wts).model(0, 0, 64, 64)
+    W = idf.World(0, st, wts, precision="bf16")
+    got = W.query(*rect).astype(np.float64)
+    W.close()
+    e = np.max(np.abs(got - ref)) / ref.std()
+    print(f"rounds (2, 2), bf16: max {e:.3e} sigma_out")
+    assert e <= 2e-2
+
+
+@pytest.mark.parametrize("rounds", [(3, 1), (2, 2)])
+def test_rounds_local_coordinate_denoiser(idf, rounds):
+    st = _rounds(synth.config1_stack(test_denoiser=3), rounds)
+    rect = (40, -23, 21, 19)
+    ref = OS.World(5, st, None).model(rect[1], rect[0], rect[3], rect[2])
+    W = idf.World(5, st, None, precision="fp32")
+    got = W.query(*rect).astype(np.float64)
+    W.close()
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
+def test_rounds_two_level_stack(idf):
+    st = _rounds(synth.small_hier_stack(steps=3), (2, 1))
+    wts = _weights(st)
+    rect = (8, -16, 32, 24)
+    ref = OS.World(1, st, wts).model(rect[1], rect[0], rect[3], rect[2])
+    W = idf.World(1, st, wts, precision="fp32")
+    got = W.query(*rect).astype(np.float64)
+    W.close()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * ref.std()
+
+
+def test_rounds_cone_and_window_count(idf):
+    # R rounds: the cone of an R-step sampler; every window of round r runs
+    # its steps, so windows_evaluated counts window-steps
+    rounds = (2, 1, 1)
+    st = _rounds(synth.config1_stack(test_denoiser=1), rounds)
+    W = idf.World(0, st, None)
+    rect = (0, 0, 48, 48)
+    counts = OK.cone_window_counts(0, 0, 48, 48, 32, 16, len(rounds))   # last round first
+    for k in range(len(rounds)):
+        assert len(W.debug_cone(*rect, 0, k)) == counts[len(rounds) - 1 - k]
+    W.query(*rect)
+    ev = W.stats()["levels"][0]["windows_evaluated"]
+    assert ev == sum(m * counts[len(rounds) - 1 - k] for k, m in enumerate(rounds))
+    W.close()
+
+
+def test_rounds_rejects_bad_grouping(idf):
+    st = synth.config1_stack(test_denoiser=1)
+    st["level"][0]["round_steps"] = (2, 1)   # sums to 3, steps = 4
+    with pytest.raises(idf.IdfError) as e:
+        idf.World(0, st, None)
+    assert e.value.status == idf.IDF_EINVAL
