@@ -453,8 +453,6 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
     // the previous copy from the staging buffer must be done before it is reused
     if (!cuda_ok(W, cudaStreamSynchronize(st), "sync")) return false;
     if (W->h_tab) cudaFreeHost(W->h_tab);
-  if (W->h_store) cudaFreeHost(W->h_store);
-  store_close(W->store);
     W->h_tab = nullptr;
     W->h_tab_cap = 0;
     if (cudaMallocHost((void**)&W->h_tab, total * 4 * 3 / 2) != cudaSuccess) {
