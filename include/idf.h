@@ -111,6 +111,23 @@ typedef struct {
    * step is blended.  round_steps is host memory, copied. */
   const int32_t* round_steps;
   int32_t n_rounds;
+  /* Per-window conditioning (App. B "Seeds and initial noise": y_i =
+   * Lambda(z, i); Sec. 5.3 feeds such a vector, the climate scalars, to the
+   * network): cond_dim = D > 0 gives window i = (row, column) the vector
+   * y_i = cond_z + cond_amp G_d(i), G_d(i) = N(seed, level, 0x7FFF0000 + d,
+   * column, row) (the seed function at counters no sampler step uses), and
+   * the UNet adds E y_i to its in-conv output, E = the (channels[0], D, 1, 1)
+   * tensor declared last among its weights.  cond_z: host, D floats. */
+  int32_t cond_dim;
+  const float* cond_z;
+  double cond_amp;
+  /* AutoGuidance (Table "Hyperparameters"): guidance = w != 0 runs a guide
+   * network of the same architecture (guide_weights, n_weights floats, host,
+   * copied) beside the main one on every window and uses F = F_guide +
+   * w (F_main - F_guide); 0 = main network only. */
+  double guidance;
+  const float* guide_weights;
+  size_t n_guide_weights;
 } idf_level_desc;
 
 /*

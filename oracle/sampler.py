@@ -37,6 +37,16 @@ lazy recursion, the cache and the cone then advance by rounds: J_r is the
 blended state after round r.  One step per round (the default) is the
 blend-every-step sampler above.
 
+Conditioning and guidance (App. B "Seeds and initial noise", Sec. 5.3,
+Table "Hyperparameters"): a level with cond_dim = D > 0 gives window i =
+(row, column) the vector y_i = Lambda(z, i) = z + cond_amp G_d(i), where z
+(cond_z) is the world's conditioning vector and G_d(i) the seed function's
+standard normal N(seed, level, COND_STEP + d, column, row) at a step counter
+no sampler step reaches; the network adds E y_i after its in-conv.  With
+guidance w != 0 a guide network (the same architecture, its own weights)
+runs beside the main one and Phi uses the AutoGuidance combination
+F = F_guide + w (F_main - F_guide) (w = 1: the main network alone).
+
 Pins: the two routes agree (Lemma 3); query-order and cache-size
 independence (Thm 1); closed forms with the test denoisers; window counts of
 Lemma 4 / Thm 2 (tests/test_oracle_sampler.py).
@@ -52,10 +62,12 @@ from . import noise as N_
 from . import schedule as S_
 from . import unet as U_
 
+COND_STEP = 0x7FFF0000  # step counter of the conditioning draws G_d(i) (+ d)
+
 
 class _LevelCommon:
     def __init__(self, seed: int, lv: dict, level_index: int, weights=None,
-                 blend_eps: float = 1e-3, parent=None):
+                 blend_eps: float = 1e-3, parent=None, guide_weights=None):
         self.seed = int(seed)
         self.lv = dict(lv)
         self.level_index = int(level_index)
@@ -73,12 +85,44 @@ class _LevelCommon:
         self.sd = float(lv["sigma_data"])
         self.W = S_.weight_2d(self.H, blend_eps)
         self.params = None
+        self.guide = None
         if int(lv.get("test_denoiser", 0)) == 0:
             self.params = U_.unpack(lv, weights)
+        self.w_guide = float(lv.get("guidance", 0.0))
+        if self.w_guide != 0.0:
+            self.guide = U_.unpack(lv, guide_weights)
+        self.cond_dim = int(lv.get("cond_dim", 0))
+        if self.cond_dim:
+            self.cond_z = np.asarray(lv["cond_z"], dtype=np.float64)
+            self.cond_amp = float(lv.get("cond_amp", 1.0))
         self.parent = parent
         self.scale = int(lv.get("scale_to_parent", 0))
         self.phi_calls = 0
         self.fmap = None      # optional xin -> F over a batch (oracle.parallel); same values
+
+    def cond_vector(self, i: int, j: int) -> np.ndarray:
+        """y_i = Lambda(z, i) for window (i, j)."""
+        g = [float(N_.normal_region(self.seed, self.level_index, COND_STEP + d, j, i, 1, 1)[0, 0])
+             for d in range(self.cond_dim)]
+        return self.cond_z + self.cond_amp * np.array(g)
+
+    def net(self, xin: np.ndarray, ys) -> np.ndarray:
+        """F of a batch of window inputs, with conditioning and guidance."""
+        def run(p):
+            F = np.empty((len(xin), self.H, self.H))
+            if self.fmap is not None and ys is None and p is self.params:
+                F[:] = self.fmap(xin)
+                return F
+            bs = 64 if self.H <= 32 else 1
+            for b0 in range(0, len(xin), bs):
+                y = None if ys is None else ys[b0:b0 + bs]
+                F[b0:b0 + bs] = U_.forward(self.lv, p, xin[b0:b0 + bs], y)[:, 0]
+            return F
+        F = run(self.params)
+        if self.guide is not None:
+            Fg = run(self.guide)
+            F = Fg + self.w_guide * (F - Fg)
+        return F
 
     def noise(self, step, y0, x0, h, w):
         return N_.normal_region(self.seed, self.level_index, step, x0, y0, w, h).astype(np.float64)
@@ -100,6 +144,9 @@ class _LevelCommon:
         if int(self.lv["in_ch"]) == 2:
             cond = np.stack([self.cond(*r) for r in rects])[:, None]
         out = [np.asarray(x, dtype=np.float64) for x in xs]
+        ys = None
+        if self.cond_dim and self.params is not None:
+            ys = np.stack([self.cond_vector((r[0] - self.o) // self.s, (r[1] - self.o) // self.s) for r in rects])
         j0 = self.round_start[k]
         for j in range(j0, j0 + self.round_steps[k]):
             c_skip, c_out, c_in = S_.edm_coeffs(self.sig[j], self.sd)
@@ -107,13 +154,10 @@ class _LevelCommon:
             if cond is not None:
                 chans.append(cond)
             xin = np.concatenate(chans, axis=1)
-            F = np.empty((len(xs), self.H, self.H))
-            if self.fmap is not None and self.params is not None:
-                F[:] = self.fmap(xin)
+            if self.params is None:
+                F = U_.forward(self.lv, None, xin)[:, 0]
             else:
-                bs = 64 if self.H <= 32 else 1
-                for b0 in range(0, len(xs), bs):
-                    F[b0:b0 + bs] = U_.forward(self.lv, self.params, xin[b0:b0 + bs])[:, 0]
+                F = self.net(xin, ys)
             self.phi_calls += len(xs)
             nxt = []
             for x, r, f in zip(out, rects, F):
@@ -220,14 +264,15 @@ class EagerLevel(_LevelCommon):
 class World:
     """A model stack (coarse level first) with lazy levels and the Laplacian decode."""
 
-    def __init__(self, seed: int, stack: dict, weights: list, capacity=None):
+    def __init__(self, seed: int, stack: dict, weights: list, capacity=None, guide_weights=None):
         self.stack = stack
         self.levels = []
         parent = None
         for li, lv in enumerate(stack["level"]):
             lvl = Level(seed, lv, li, weights=weights[li] if weights else None,
                         blend_eps=stack.get("blend_eps", 1e-3), parent=parent,
-                        capacity=capacity)
+                        capacity=capacity,
+                        guide_weights=guide_weights[li] if guide_weights else None)
             self.levels.append(lvl)
             parent = lvl
 

@@ -27,6 +27,12 @@ fixed for them (everything the stack description leaves open):
   learning framework; parameters are declared in the order listed above
   (per ResBlock: conv1, conv2, then shortcut if any; attention: qkv, proj).
 
+Per-window conditioning (App. B "Seeds and initial noise": y_i = Lambda(z, i);
+Sec. 5.3 injects such a vector, the climate scalars, alongside the noise
+embedding): with cond_dim = D > 0 the network takes a vector y of D values
+per window and adds E y, E a (c0, D) linear embedding declared last among
+the parameters ("cond_embed"), as a per-channel bias to the in-conv output.
+
 Test denoisers (closed-form pins of the sampler, not networks): 1 = constant
 F = 0.5; 2 = identity F = sum of input channels; 3 = local coordinate
 F = sum of input channels + u/H - 2 v/H (u row, v column inside the window).
@@ -69,6 +75,8 @@ def param_shapes(lv: dict):
         rb(f"dec{l}", prev + ch[l], ch[l])
         prev = ch[l]
     out.append(("out_conv", (int(lv["out_ch"]), prev, 3, 3)))
+    if int(lv.get("cond_dim", 0)) > 0:
+        out.append(("cond_embed", (ch[0], int(lv["cond_dim"]), 1, 1)))
     return out
 
 
@@ -150,8 +158,14 @@ def attention(x, p, groups, heads):
     return x + conv(o, p["attn.proj"])
 
 
-def forward(lv: dict, p: dict, x: np.ndarray) -> np.ndarray:
-    """F(x) for a batch of windows x (B, in_ch, H, W) -> (B, out_ch, H, W)."""
+def cond_bias(p: dict, y: np.ndarray) -> np.ndarray:
+    """Per-window bias E y (B, c0) of conditioning vectors y (B, D)."""
+    return np.asarray(y, dtype=np.float64) @ p["cond_embed"][:, :, 0, 0].T
+
+
+def forward(lv: dict, p: dict, x: np.ndarray, y=None) -> np.ndarray:
+    """F(x) for a batch of windows x (B, in_ch, H, W) -> (B, out_ch, H, W);
+    y (B, cond_dim): the windows' conditioning vectors (cond_dim > 0)."""
     td = int(lv.get("test_denoiser", 0))
     x = np.asarray(x, dtype=np.float64)
     if td:
@@ -159,6 +173,8 @@ def forward(lv: dict, p: dict, x: np.ndarray) -> np.ndarray:
     L = int(lv["levels"])
     G = int(lv["gn_groups"])
     h = conv(x, p["in_conv"])
+    if y is not None:
+        h = h + cond_bias(p, y)[:, :, None, None]
     skips = []
     for l in range(L):
         h = resblock(h, p, f"enc{l}", G)

@@ -54,6 +54,8 @@ class idf_level_desc(C.Structure):
         ("sigma_data", C.c_double),
         ("scale_to_parent", C.c_int32), ("test_denoiser", C.c_int32),
         ("round_steps", C.POINTER(C.c_int32)), ("n_rounds", C.c_int32),
+        ("cond_dim", C.c_int32), ("cond_z", C.POINTER(C.c_float)), ("cond_amp", C.c_double),
+        ("guidance", C.c_double), ("guide_weights", C.POINTER(C.c_float)), ("n_guide_weights", C.c_size_t),
     ]
 
 
@@ -143,7 +145,7 @@ class _Keep:
         self.refs = []
 
 
-def level_desc(lv: dict, weights=None, keep: Optional[_Keep] = None) -> idf_level_desc:
+def level_desc(lv: dict, weights=None, keep: Optional[_Keep] = None, guide=None) -> idf_level_desc:
     import numpy as np
     keep = keep or _Keep()
     ch = (C.c_int32 * len(lv["channels"]))(*lv["channels"])
@@ -167,15 +169,29 @@ def level_desc(lv: dict, weights=None, keep: Optional[_Keep] = None) -> idf_leve
         keep.refs.append(arr)
         d.round_steps = arr
         d.n_rounds = len(rs)
+    if int(lv.get("cond_dim", 0)) > 0:
+        z = np.ascontiguousarray(lv["cond_z"], dtype=np.float32)
+        keep.refs.append(z)
+        d.cond_dim = int(lv["cond_dim"])
+        d.cond_z = z.ctypes.data_as(C.POINTER(C.c_float))
+        d.cond_amp = float(lv.get("cond_amp", 1.0))
+    d.guidance = float(lv.get("guidance", 0.0))
+    if guide is not None:
+        g = np.ascontiguousarray(guide, dtype=np.float32)
+        keep.refs.append(g)
+        d.guide_weights = g.ctypes.data_as(C.POINTER(C.c_float))
+        d.n_guide_weights = g.size
     return d
 
 
-def model_stack(st: dict, weights: Optional[Sequence] = None, keep: Optional[_Keep] = None) -> idf_model_stack:
+def model_stack(st: dict, weights: Optional[Sequence] = None, keep: Optional[_Keep] = None,
+                guide_weights: Optional[Sequence] = None) -> idf_model_stack:
     keep = keep or _Keep()
     n = len(st["level"])
     arr = (idf_level_desc * n)()
     for i, lv in enumerate(st["level"]):
-        arr[i] = level_desc(lv, None if weights is None else weights[i], keep)
+        arr[i] = level_desc(lv, None if weights is None else weights[i], keep,
+                            None if guide_weights is None else guide_weights[i])
     keep.refs.append(arr)
     s = idf_model_stack()
     s.n_levels = n
@@ -234,11 +250,12 @@ class World:
     def __init__(self, seed: int, stack: dict, weights: Optional[Sequence] = None,
                  precision: str = "fp32", cache_bytes: int = 0, device: int = 0,
                  workspace_bytes: int = 0, max_batch: int = 0, profile: bool = False,
-                 wait_budget_cycles: int = 0, groupnorm_in_conv: bool = False):
+                 wait_budget_cycles: int = 0, groupnorm_in_conv: bool = False,
+                 guide_weights: Optional[Sequence] = None):
         L = lib()
         self._keep = _Keep()
         self.stack = stack
-        st = model_stack(stack, weights, self._keep)
+        st = model_stack(stack, weights, self._keep, guide_weights)
         o = idf_world_opts()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.cache_bytes, o.device, o.workspace_bytes, o.max_batch = cache_bytes, device, workspace_bytes, max_batch

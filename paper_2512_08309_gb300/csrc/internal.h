@@ -68,6 +68,14 @@ struct WindowStepArgs {
 };
 void launch_window_step(const WindowStepArgs& a, cudaStream_t st);
 
+// Per-window conditioning bias: window b = (i, j) gets y_d = z_d + amp
+// N(seed, level, COND_STEP + d, j, i) and bias[b][c] = sum_d E[c][d] y_d.
+constexpr uint32_t COND_STEP = 0x7FFF0000u;
+void launch_cond_bias(const int32_t* win_ij, int n, uint64_t seed, uint32_t level, const float* z, float amp,
+                      const float* E, int D, int C, float* bias, cudaStream_t st);
+// AutoGuidance: F = Fg + w (F - Fg), n values
+void launch_guidance(float* F, const float* Fg, int64_t n, float w, cudaStream_t st);
+
 struct BlendArgs {
   const float* pool;
   float* pool_out;
@@ -193,6 +201,7 @@ struct UNetDesc {
   int levels;
   std::vector<int> ch;
   int in_ch, out_ch, groups, attn, heads, window;
+  int cond_dim = 0;  // > 0: a conditioning embedding (ch[0], cond_dim, 1, 1) declared last
 };
 // Shapes (Cout, Cin, kh, kw) in declaration order.
 std::vector<std::vector<int>> unet_param_shapes(const UNetDesc& d);
@@ -205,8 +214,10 @@ size_t unet_arena_bytes(const UNetDesc& d, int precision, int max_batch);
 void unet_destroy(UNet* u);
 int unet_max_batch(const UNet* u);
 size_t unet_bytes_per_window(const UNetDesc& d, int precision);
-// x_in NHWC float32 [n][H][H][in_ch] -> F [n][H][H] float32 (out_ch = 1).
-bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err);
+// x_in NHWC float32 [n][H][H][in_ch] -> F [n][H][H] float32 (out_ch = 1);
+// bias: optional [n][ch[0]] per-window conditioning bias added after the in-conv.
+bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err,
+                  const float* bias = nullptr);
 int64_t unet_launches(const UNet* u);
 // device status word set by bounded device-side waits that ran out
 int* unet_status(const UNet* u);
@@ -264,7 +275,7 @@ SmallNet* small_net_create(const UNetDesc& d, const float* w_host, bool fp8, Err
 void small_net_destroy(SmallNet* s);
 // F (n, 32, 32) float32 of x (n, 32, 32, in_ch) NHWC float32
 bool small_net_forward(const SmallNet* s, const float* x, int n, float* F, int* status, long long wait_limit,
-                       cudaStream_t st, std::string* err);
+                       cudaStream_t st, std::string* err, const float* bias = nullptr);
 
 // Persistent tile store (store.cpp): chunk files of finalized tiles in a
 // directory, tied to a world identity by a manifest.

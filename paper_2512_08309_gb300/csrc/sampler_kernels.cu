@@ -103,6 +103,39 @@ void launch_window_step(const WindowStepArgs& a, cudaStream_t st) {
   window_step_kernel<<<grid_for(n, 256), 256, 0, st>>>(a);
 }
 
+// ------------------------------------------------------------ conditioning
+__global__ void cond_bias_kernel(const int32_t* win_ij, int n, uint64_t seed, uint32_t level, const float* z,
+                                 float amp, const float* E, int D, int C, float* bias) {
+  const int64_t total = (int64_t)n * C;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / C), c = (int)(t % C);
+    const int64_t i = win_ij[2 * b], j = win_ij[2 * b + 1];
+    float acc = 0.0f;
+    for (int d = 0; d < D; ++d) {
+      const float y = __fadd_rn(z[d], __fmul_rn(amp, normal_at(seed, level, COND_STEP + (uint32_t)d, j, i)));
+      acc = __fadd_rn(acc, __fmul_rn(E[c * D + d], y));
+    }
+    bias[t] = acc;
+  }
+}
+
+void launch_cond_bias(const int32_t* win_ij, int n, uint64_t seed, uint32_t level, const float* z, float amp,
+                      const float* E, int D, int C, float* bias, cudaStream_t st) {
+  cond_bias_kernel<<<grid_for((int64_t)n * C, 256), 256, 0, st>>>(win_ij, n, seed, level, z, amp, E, D, C, bias);
+}
+
+__global__ void guidance_kernel(float* F, const float* Fg, int64_t n, float w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = Fg[i];
+    F[i] = __fadd_rn(g, __fmul_rn(w, __fsub_rn(F[i], g)));
+  }
+}
+
+void launch_guidance(float* F, const float* Fg, int64_t n, float w, cudaStream_t st) {
+  guidance_kernel<<<grid_for(n, 256), 256, 0, st>>>(F, Fg, n, w);
+}
+
 // ------------------------------------------------------------------ blend
 // One step of Eq. 2 for the missing tiles of J_{k+1}, in the fused form
 //   J_{k+1} = c_skip J_k + c_out (sum_i W_i F_i) / B + sigma_{k+1} N(k+1)

@@ -1617,6 +1617,7 @@ std::vector<std::vector<int>> unet_param_shapes(const UNetDesc& d) {
     prev = d.ch[l];
   }
   s.push_back({d.out_ch, prev, 3, 3});
+  if (d.cond_dim > 0) s.push_back({d.ch[0], d.cond_dim, 1, 1});  // conditioning embedding E
   return s;
 }
 
@@ -2489,13 +2490,25 @@ bool resblock(Ctx& c, size_t& wi, const LevelBufs& b, const float* X, int cin, i
   return conv_run<TA>(c, c2, b.T1, false, res, Y, b.H, sp ? b.T1lo : nullptr, bsY);
 }
 
+// y[b][p][c] += bias[b][c] over hw pixels of C channels per window
+__global__ void add_bias_kernel(float* y, const float* bias, int n, int hw, int C) {
+  const int64_t total = (int64_t)n * hw * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __fadd_rn(y[i], bias[(i / ((int64_t)hw * C)) * C + i % C]);
+}
+
 template <typename TA>
-bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err) {
+bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err, const float* bias) {
   Ctx c{u, n, st, err};
   const UNetDesc& d = u->d;
   const int L = d.levels;
   size_t wi = 0;
   conv_run<TA>(c, u->convs[wi++], x_in, true, nullptr, (float*)u->lv[0].P, d.window);
+  if (bias) {
+    const int64_t tot = (int64_t)n * d.window * d.window * d.ch[0];
+    add_bias_kernel<<<grid1d(tot, 256), 256, 0, st>>>((float*)u->lv[0].P, bias, n, d.window * d.window, d.ch[0]);
+    u->launches++;
+  }
   int prev = d.ch[0];
   // which of SK / M hold block partials written by their convolution
   bool sk_st[8] = {false}, m_st[8] = {false};
@@ -2604,7 +2617,7 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
 
 }  // namespace
 
-bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err) {
+bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err* err, const float* bias) {
   if (n > u->max_batch) {
     err->code = 7;
     err->msg = "UNet batch larger than its workspace";
@@ -2621,7 +2634,7 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
     fl += 2.0 * 1024 * 9 * 16;                                       // output conv
     const int pr = u->prof ? u->prof->begin(PK_CONV_TC, st, fl * n, (double)n * 1024 * 4 * (d.in_ch + 1)) : -1;
     std::string e;
-    const bool ok = small_net_forward(u->small, x_in, n, F, u->status, u->wait_limit, st, &e);
+    const bool ok = small_net_forward(u->small, x_in, n, F, u->status, u->wait_limit, st, &e, bias);
     if (u->prof) u->prof->end(pr, st);
     u->launches++;
     if (!ok) {
@@ -2630,9 +2643,9 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
     }
     return ok;
   }
-  if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err);
-  if (u->precision == 4) return forward_t<tf32>(u, x_in, n, F, st, err);
-  return forward_t<float>(u, x_in, n, F, st, err);
+  if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err, bias);
+  if (u->precision == 4) return forward_t<tf32>(u, x_in, n, F, st, err, bias);
+  return forward_t<float>(u, x_in, n, F, st, err, bias);
 }
 
 // ------------------------------------------------------------ float32 building blocks

@@ -77,6 +77,7 @@ struct SmallArgs {
   const int* wofs;         // [NCONV] first block of each convolution
   const float* dqw;        // [NCONV][16] weight dequantisation scales
   const float* w_in;       // [9][in_ch][16] input convolution, float32
+  const float* bias;       // [n][16] per-window conditioning bias after the input conv, or null
   int n, in_ch, fp8, n_blocks;
   int* status;
   long long wait_limit;
@@ -454,6 +455,9 @@ __global__ void __launch_bounds__(NTHR, 1) unet16_kernel(SmallArgs a) {
             for (int c = 0; c < 16; ++c) v[c] = fmaf(xv, wr[c], v[c]);
           }
         }
+        if (a.bias)
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] += a.bias[(size_t)wi * 16 + c];
       }
       tst16(tmem + lane_off + TM_A + 16 * m, v);
     }
@@ -825,7 +829,7 @@ void small_net_destroy(SmallNet* s) {
 
 // F (n windows, 32 x 32) of x (n, 32, 32, in_ch) NHWC float32
 bool small_net_forward(const SmallNet* s, const float* x, int n, float* F, int* status, long long wait_limit,
-                       cudaStream_t st, std::string* err) {
+                       cudaStream_t st, std::string* err, const float* bias) {
   if (n <= 0) return true;
   const size_t smem = (size_t)OPB_BYTES + (size_t)s->n_blocks * BLK +
                       (16 * 16 * 16 + NCONV * 16 + 9 * 2 * 16 + 64 + 8) * sizeof(float);
@@ -852,6 +856,7 @@ bool small_net_forward(const SmallNet* s, const float* x, int n, float* F, int* 
   a.wofs = s->wofs;
   a.dqw = s->dqw;
   a.w_in = s->w_in;
+  a.bias = bias;
   a.n = n;
   a.in_ch = s->in_ch;
   a.fp8 = s->fp8;

@@ -127,6 +127,12 @@ struct Level {
   TileCache cache;
   int64_t windows_evaluated = 0, tiles_computed = 0;
   int64_t store_reads = 0, store_writes = 0;
+  // conditioning vector and embedding (cond_dim > 0), AutoGuidance guide
+  std::vector<float> condz;
+  float* d_condE = nullptr;
+  float* d_condz = nullptr;
+  UNet* guide = nullptr;
+  float w_guide = 0.0f;
 };
 
 }  // namespace
@@ -144,6 +150,8 @@ struct idf_world {
   float* F = nullptr; size_t F_cap = 0;
   float* x_in = nullptr; size_t x_cap = 0;
   float* xs = nullptr; size_t xs_cap = 0;          // window states of multi-step rounds
+  float* bias = nullptr; size_t bias_cap = 0;      // per-window conditioning biases
+  float* Fg = nullptr; size_t Fg_cap = 0;          // guide network outputs
   int32_t* tab = nullptr; size_t tab_cap = 0;
   float* dense = nullptr; size_t dense_cap = 0;    // assembled level results
   float* dec = nullptr; size_t dec_cap = 0;        // decode scratch
@@ -224,6 +232,7 @@ UNetDesc unet_desc(const idf_level_desc& d) {
   u.attn = d.attn_at_bottom;
   u.heads = d.attn_heads;
   u.window = d.window;
+  u.cond_dim = d.cond_dim;
   return u;
 }
 
@@ -242,6 +251,8 @@ std::string check_level(const idf_level_desc& d, int index) {
   if (d.scale_to_parent > 0 && index == 0) return bad("the first level has no parent");
   if (d.test_denoiser < 0 || d.test_denoiser > 3) return bad("test_denoiser must be 0..3");
   if (d.n_rounds < 0 || (d.n_rounds > 0 && !d.round_steps)) return bad("round_steps missing");
+  if (d.cond_dim < 0 || d.cond_dim > 64 || (d.cond_dim > 0 && !d.cond_z)) return bad("cond_dim in [0, 64] with cond_z");
+  if (!(d.guidance == d.guidance)) return bad("guidance must be a number");
   if (d.n_rounds > 0) {
     int64_t sum = 0;
     for (int r = 0; r < d.n_rounds; ++r) {
@@ -510,6 +521,15 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
       W->prof.end(pr, st);
       W->launches++;
       float* Fb = W->F + (size_t)b0 * H * H;
+      const float* bias = nullptr;
+      if (L.d.cond_dim > 0 && L.unet) {
+        const int c0 = L.d.channels[0];
+        if (!grow(W, &W->bias, &W->bias_cap, (size_t)nb * c0, "conditioning biases")) return false;
+        launch_cond_bias(g.win_ij, nb, W->seed, (uint32_t)L.index, L.d_condz, (float)L.d.cond_amp, L.d_condE,
+                         L.d.cond_dim, c0, W->bias, st);
+        W->launches++;
+        bias = W->bias;
+      }
       for (int i = 0; i < m; ++i) {
         const int j = j0 + i;
         if (L.d.test_denoiser) {
@@ -520,12 +540,26 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
         } else {
           Err e;
           const int64_t l0 = unet_launches(L.unet);
-          if (!unet_forward(L.unet, W->x_in, nb, Fb, st, &e)) {
+          if (!unet_forward(L.unet, W->x_in, nb, Fb, st, &e, bias)) {
             W->last_error = e.msg;
             W->poisoned = e.code == 3;
             return false;
           }
           W->launches += unet_launches(L.unet) - l0;
+          if (L.guide) {
+            // AutoGuidance: the guide network on the same inputs, then
+            // F = F_guide + w (F_main - F_guide)
+            if (!grow(W, &W->Fg, &W->Fg_cap, (size_t)nb * H * H, "guide outputs")) return false;
+            const int64_t g0 = unet_launches(L.guide);
+            if (!unet_forward(L.guide, W->x_in, nb, W->Fg, st, &e, bias)) {
+              W->last_error = e.msg;
+              W->poisoned = e.code == 3;
+              return false;
+            }
+            W->launches += unet_launches(L.guide) - g0;
+            launch_guidance(Fb, W->Fg, (int64_t)nb * H * H, L.w_guide, st);
+            W->launches++;
+          }
         }
         if (m > 1) {
           // window-local update; the round's last step leaves D in F
@@ -1028,6 +1062,11 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
       const double dv[4] = {d.sigma_max, d.sigma_min, d.rho, d.sigma_data};
       mix(dv, sizeof dv);
       if (d.weights && d.test_denoiser == 0) mix(d.weights, d.n_weights * sizeof(float));
+      mix(&d.cond_dim, sizeof d.cond_dim);
+      if (d.cond_dim > 0 && d.cond_z) mix(d.cond_z, (size_t)d.cond_dim * sizeof(float));
+      const double cv[2] = {d.cond_amp, d.guidance};
+      mix(cv, sizeof cv);
+      if (d.guidance != 0.0 && d.guide_weights) mix(d.guide_weights, d.n_guide_weights * sizeof(float));
     }
     W->identity = h;
   }
@@ -1041,6 +1080,8 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
       L.d.channels = L.ch.data();
     }
     L.d.weights = nullptr;
+    L.d.cond_z = nullptr;
+    L.d.guide_weights = nullptr;
     L.index = i;
     L.H = L.d.window;
     L.s = L.d.stride;
@@ -1108,6 +1149,24 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
       }
       unet_set_prof(L.unet, &W->prof);
       unet_set_options(L.unet, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles);
+      const idf_level_desc& dsrc = stack->level[i];
+      if (dsrc.cond_dim > 0) {
+        // the embedding E is the last (channels[0], cond_dim, 1, 1) tensor
+        const size_t ne = (size_t)L.d.channels[0] * dsrc.cond_dim;
+        L.condz.assign(dsrc.cond_z, dsrc.cond_z + dsrc.cond_dim);
+        if (cudaMalloc(&L.d_condE, ne * 4) != cudaSuccess || cudaMalloc(&L.d_condz, dsrc.cond_dim * 4) != cudaSuccess ||
+            cudaMemcpy(L.d_condE, dsrc.weights + nw - ne, ne * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(L.d_condz, L.condz.data(), dsrc.cond_dim * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+          return bail(IDF_ENOMEM);
+      }
+      if (dsrc.guidance != 0.0) {
+        if (!dsrc.guide_weights || dsrc.n_guide_weights != nw) return bail(IDF_EMODEL);
+        L.guide = unet_create(ud, dsrc.guide_weights, opts->precision, batches[i], &e, W->arena, W->arena_bytes);
+        if (!L.guide) return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
+        unet_set_prof(L.guide, &W->prof);
+        unet_set_options(L.guide, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles);
+        L.w_guide = (float)dsrc.guidance;
+      }
     }
   }
   if (stack->laplacian) {
@@ -1131,11 +1190,14 @@ void idf_world_destroy(idf_world* W) {
   if (W->st) cudaStreamSynchronize(W->st);
   for (auto& L : W->lv) {
     unet_destroy(L.unet);
+    unet_destroy(L.guide);
+    cudaFree(L.d_condE);
+    cudaFree(L.d_condz);
     cudaFree(L.d_w1);
     cudaFree(L.d_invB1);
     cudaFree(L.cache.pool);
   }
-  cudaFree(W->F); cudaFree(W->x_in); cudaFree(W->xs); cudaFree(W->tab); cudaFree(W->dense); cudaFree(W->dec);
+  cudaFree(W->F); cudaFree(W->x_in); cudaFree(W->xs); cudaFree(W->bias); cudaFree(W->Fg); cudaFree(W->tab); cudaFree(W->dense); cudaFree(W->dec);
   cudaFree(W->outbuf); cudaFree(W->d_taps); cudaFree(W->d_fixture); cudaFree(W->d_err); cudaFree(W->arena);
   if (W->h_tab) cudaFreeHost(W->h_tab);
   if (W->h_store) cudaFreeHost(W->h_store);

@@ -139,6 +139,31 @@ def weights(shapes: Iterable[Sequence[int]], weight_seed: int = 0,
     return np.concatenate(parts)
 
 
+def guide_weights(main: np.ndarray, shapes: Iterable[Sequence[int]], level_index: int = 0,
+                  mix: float = 0.3) -> np.ndarray:
+    """Weights of an AutoGuidance guide network for a synthetic main network:
+    a degraded copy, (1 - mix) main + mix (an independent draw of the same
+    shapes, weight seed 1).  The paper's guides are smaller or less trained
+    versions of the main model (Table "Hyperparameters"); none exist here."""
+    other = weights(shapes, 1, level_index)
+    return ((1.0 - mix) * np.asarray(main, dtype=np.float64) + mix * other).astype(np.float32)
+
+
+def conditioned(st: dict, dim: int = 4, z=(0.5, -1.0, 0.25, 2.0), amp: float = 0.3,
+                guidance: float = 0.0, levels=None) -> dict:
+    """A copy of a stack whose levels (all, or the indices given) take a
+    per-window conditioning vector of `dim` values around z (and, with
+    guidance != 0, an AutoGuidance guide network)."""
+    st = copy.deepcopy(st)
+    for i, lv in enumerate(st["level"]):
+        if levels is None or i in levels:
+            lv["cond_dim"] = int(dim)
+            lv["cond_z"] = tuple(float(v) for v in z[:dim])
+            lv["cond_amp"] = float(amp)
+            lv["guidance"] = float(guidance)
+    return st
+
+
 # ---------------------------------------------------------------------------
 # Window inputs for per-window network tests
 # ---------------------------------------------------------------------------

@@ -1,0 +1,69 @@
+"""Per-window conditioning vectors y_i = Lambda(z, i) and AutoGuidance
+against the FP64 oracle: the 16-channel network (FP32 SIMT and the fused
+BF16 kernel, whose input convolution adds the conditioning bias), a
+two-level stack conditioned at its fine level, and the full-width fine UNet
+on the tensor cores (TF32)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import sampler as OS
+from oracle import unet as OU
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def idf():
+    import paper_2512_08309_gb300 as m
+    m.lib()
+    return m
+
+
+def _weights(st, guided=False):
+    w, g = [], []
+    for i, lv in enumerate(st["level"]):
+        shapes = [s for _, s in OU.param_shapes(lv)]
+        w.append(synth.weights(shapes, 0, i))
+        g.append(synth.guide_weights(w[-1], shapes, i))
+    return w, (g if guided else None)
+
+
+def _run(idf, st, w, g, rect, precision):
+    ref = OS.World(3, st, w, guide_weights=g).model(rect[1], rect[0], rect[3], rect[2])
+    W = idf.World(3, st, w, precision=precision, guide_weights=g)
+    got = W.query(*rect).astype(np.float64)
+    W.close()
+    return float(np.max(np.abs(got - ref)) / ref.std())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 2e-2)])
+def test_conditioned_guided_16_channel(idf, precision, tol):
+    st = synth.conditioned(synth.config1_stack(), dim=4, guidance=2.15)
+    w, g = _weights(st, guided=True)
+    e = _run(idf, st, w, g, (-24, 8, 64, 48), precision)
+    print(f"conditioned + AutoGuidance 2.15, {precision}: max {e:.3e} sigma_out")
+    assert e <= tol
+
+
+def test_conditioned_two_level_fine(idf):
+    st = synth.conditioned(synth.small_hier_stack(steps=3), dim=3, levels=[1])
+    w, _ = _weights(st)
+    e = _run(idf, st, w, None, (8, -16, 32, 24), "fp32")
+    assert e <= 1e-4
+
+
+def test_conditioned_full_width_tf32(idf):
+    st = synth.conditioned(synth.config2_stack(steps=2), dim=4, levels=[1])
+    w, _ = _weights(st)
+    e = _run(idf, st, w, None, (0, 0, 64, 64), "tf32")
+    print(f"conditioned full-width fine UNet, tf32: max {e:.3e} sigma_out")
+    assert e <= 2e-2
+
+
+def test_guidance_needs_guide_weights(idf):
+    st = synth.conditioned(synth.config1_stack(), dim=4, guidance=2.0)
+    w, _ = _weights(st)
+    with pytest.raises(idf.IdfError) as e:
+        idf.World(0, st, w)
+    assert e.value.status == idf.IDF_EMODEL

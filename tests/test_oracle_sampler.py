@@ -277,3 +277,49 @@ def test_rounds_lazy_equals_eager_and_cone_counts():
     counts = K.cone_window_counts(0, 0, 32, 32, 32, 16, 2)
     assert counts == [(2 + 1) ** 2, (2 + 3) ** 2]
     assert lz.levels[0].phi_calls == 2 * sum(counts)
+
+
+
+# ----------------------------------------------------------- conditioning and AutoGuidance
+
+def _cond_setup(w, steps=1, z=(0.5, -1.0, 0.25, 2.0), amp=0.3):
+    st = synth.with_steps(synth.conditioned(synth.config1_stack(), dim=4, z=z, amp=amp, guidance=w), steps)
+    lv = st["level"][0]
+    shapes = [s for _, s in U.param_shapes(lv)]
+    main = synth.weights(shapes, 0, 0)
+    guide = synth.guide_weights(main, shapes, 0)
+    return st, main, guide
+
+
+def test_guidance_is_affine_in_the_scale_for_one_step():
+    # one blended step: J_1 = c_skip J_0 + c_out blend(F_g + w (F_m - F_g)),
+    # so J_1(w) = (1 - w) J_1(guide) + w J_1(main) exactly (blending is linear)
+    rect = (-9, 5, 20, 23)
+    st2, main, guide = _cond_setup(2.15)
+    got = S.World(4, st2, [main], guide_weights=[guide]).model(*rect)
+    st0, _, _ = _cond_setup(0.0)
+    j_main = S.World(4, st0, [main]).model(*rect)
+    j_guide = S.World(4, st0, [guide]).model(*rect)
+    ref = (1 - 2.15) * j_guide + 2.15 * j_main
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # w = 1 is the main network alone
+    st1, _, _ = _cond_setup(1.0)
+    j1 = S.World(4, st1, [main], guide_weights=[guide]).model(*rect)
+    assert np.max(np.abs(j1 - j_main)) <= 1e-12 * np.max(np.abs(j_main))
+
+
+def test_zero_conditioning_equals_the_unconditioned_network():
+    # z = 0 and amp = 0 give y_i = 0, so E y_i = 0 whatever E is
+    st, main, _ = _cond_setup(0.0, steps=2, z=(0.0, 0.0, 0.0, 0.0), amp=0.0)
+    plain = synth.with_steps(synth.config1_stack(), 2)
+    n_plain = sum(int(np.prod(s)) for _, s in U.param_shapes(plain["level"][0]))
+    rect = (3, -7, 17, 19)
+    a = S.World(1, st, [main]).model(*rect)
+    b = S.World(1, plain, [main[:n_plain]]).model(*rect)
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+    # with a non-zero vector the result moves, and differs between windows
+    st_c, _, _ = _cond_setup(0.0, steps=2)
+    c = S.World(1, st_c, [main]).model(*rect)
+    assert np.max(np.abs(c - b)) > 1e-3 * np.max(np.abs(b))
+    lvl = S.World(1, st_c, [main]).levels[0]
+    assert not np.allclose(lvl.cond_vector(0, 0), lvl.cond_vector(0, 1))

@@ -10,8 +10,9 @@ import synth
 from oracle import unet as U
 
 
-def torch_forward(lv, p, x):
-    """The same network written with torch.nn.functional layers (FP64)."""
+def torch_forward(lv, p, x, y=None):
+    """The same network written with torch.nn.functional layers (FP64);
+    y: per-window conditioning vectors embedded by F.linear as a bias."""
     G = lv["gn_groups"]
     t = {k: torch.from_numpy(v) for k, v in p.items()}
 
@@ -27,6 +28,8 @@ def torch_forward(lv, p, x):
         return a + (conv(h, t[name + ".skip"]) if name + ".skip" in t else h)
 
     h = conv(torch.from_numpy(x), t["in_conv"])
+    if y is not None:
+        h = h + TF.linear(torch.from_numpy(y), t["cond_embed"][:, :, 0, 0])[:, :, None, None]
     skips = []
     L = lv["levels"]
     for l in range(L):
@@ -127,3 +130,17 @@ def test_upsampled_branch_phase_identity():
     sk_ref = U.conv(cat, wsk)
     sk = U.up2(U.conv(a, wsk[:, :Ca])) + U.conv(b, wsk[:, Ca:])
     assert np.allclose(sk, sk_ref, rtol=0, atol=1e-12)
+
+
+def test_conditioning_bias_matches_torch_linear():
+    # the per-window conditioning vector enters as E y added after the in-conv
+    st = synth.conditioned(synth.config1_stack(), dim=4)
+    lv = st["level"][0]
+    p = U.unpack(lv, synth.weights([s for _, s in U.param_shapes(lv)], 0, 0))
+    x = synth.window_batch(3, 1, 32, seed=2).astype(np.float64)
+    y = np.random.default_rng(0).standard_normal((3, 4))
+    got = U.forward(lv, p, x, y)
+    ref = np.asarray(torch_forward(lv, p, x, y))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # and it changes the output (a dropped bias would not)
+    assert np.max(np.abs(got - U.forward(lv, p, x))) > 1e-3 * np.max(np.abs(ref))
