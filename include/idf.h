@@ -123,8 +123,9 @@ typedef struct {
   double cond_amp;
   /* AutoGuidance (Table "Hyperparameters"): guidance = w != 0 runs a guide
    * network of the same architecture (guide_weights, n_weights floats, host,
-   * copied) beside the main one on every window and uses F = F_guide +
-   * w (F_main - F_guide); 0 = main network only. */
+   * copied; with cond_dim > 0 it embeds y_i with its own E) beside the main
+   * one on every window and uses F = F_guide + w (F_main - F_guide); 0 =
+   * main network only. */
   double guidance;
   const float* guide_weights;
   size_t n_guide_weights;
@@ -172,6 +173,10 @@ typedef struct {
   uint64_t device_wait_budget_cycles; /* clock64 cycles a bounded device-side wait of the
                                        tensor-core kernels may take before it gives up and
                                        the query returns IDF_ETIMEOUT; 0 = 1e9 (about 0.5 s) */
+  int32_t autotune;                 /* 1: the first launch of every tensor-core convolution (per
+                                       layer, geometry and batch class) times each valid tile
+                                       shape (BN, MT, staging) and keeps the fastest; results are
+                                       the same bit for bit; 0 = built-in shapes */
   int32_t groupnorm_in_conv;        /* IDF_TF32: 1 applies GroupNorm and SiLU inside the
                                        tensor-core convolutions' operand path (no normalised
                                        operand in memory); 0 (default) runs them as separate

@@ -73,7 +73,7 @@ class idf_world_opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("cache_bytes", C.c_size_t), ("device", C.c_int32),
         ("workspace_bytes", C.c_size_t), ("max_batch", C.c_int32), ("profile", C.c_int32),
-        ("device_wait_budget_cycles", C.c_uint64), ("groupnorm_in_conv", C.c_int32),
+        ("device_wait_budget_cycles", C.c_uint64), ("autotune", C.c_int32), ("groupnorm_in_conv", C.c_int32),
     ]
 
 
@@ -251,7 +251,7 @@ class World:
                  precision: str = "fp32", cache_bytes: int = 0, device: int = 0,
                  workspace_bytes: int = 0, max_batch: int = 0, profile: bool = False,
                  wait_budget_cycles: int = 0, groupnorm_in_conv: bool = False,
-                 guide_weights: Optional[Sequence] = None):
+                 guide_weights: Optional[Sequence] = None, autotune: bool = False):
         L = lib()
         self._keep = _Keep()
         self.stack = stack
@@ -262,6 +262,7 @@ class World:
         o.profile = 1 if profile else 0
         o.device_wait_budget_cycles = int(wait_budget_cycles)
         o.groupnorm_in_conv = 1 if groupnorm_in_conv else 0
+        o.autotune = 1 if autotune else 0
         h = C.c_void_p()
         _check(L.idf_world_create(C.c_uint64(seed), C.byref(st), C.byref(o), C.byref(h)), "idf_world_create")
         self._h = h

@@ -741,6 +741,28 @@ bool conv_tc_supported(int cin, int cout, int ks) {
          (cout <= 256 || cout % 256 == 0);
 }
 
+std::vector<TcTile> conv_tc_tiles(int H, int W, int Cin, int Cout, int ks, bool split, bool /*xf*/,
+                                  const TcGeom* geom) {
+  std::vector<TcTile> out;
+  if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) return out;
+  for (int bn : {64, 128, 256}) {
+    if (bn > Cout || Cout % bn) continue;
+    const bool dxr_ok = ks == 3 && W == 128 && bn == 64 && (!geom || (geom->oy == -1 && geom->ox == -1));
+    const bool mt2_ok = ((int64_t)H * W / BM) % 2 == 0 && !(split && bn == 64) && bn <= 128;
+    for (int mt = 1; mt <= (mt2_ok ? 2 : 1); ++mt)
+      for (int dx = 0; dx <= (dxr_ok ? 1 : 0); ++dx) {
+        // split kernels exist for BN = 64 (MT 1), 128 (MT 1, 2), 256 (MT 1)
+        if (split && bn == 64 && mt == 2) continue;
+        TcTile t;
+        t.bn = bn;
+        t.mt = mt;
+        t.dxr = dx;
+        out.push_back(t);
+      }
+  }
+  return out;
+}
+
 bool conv_tc_shape_ok(int H, int W) {
   return W >= 1 && W <= 128 && 128 % W == 0 && ((int64_t)H * W) % 128 == 0 && 128 / W <= H;
 }
@@ -749,7 +771,7 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
                      cudaStream_t st, std::string* err, const void* x2, const void* w2, const void* x2_lo,
                      const void* w2_lo, int Cin2, bool tf32, const TcGeom* geom, const TcXf* xf,
-                     long long wait_limit) {
+                     long long wait_limit, const TcTile* tile) {
   if (!conv_tc_supported(Cin, Cout, ks) || !conv_tc_shape_ok(H, W)) {
     *err = "shape not supported by the tensor-core convolution";
     return false;
@@ -764,7 +786,14 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
     *err = "cuTensorMapEncodeTiled unavailable";
     return false;
   }
-  const int BN = Cout <= 256 ? Cout : 256;
+  int BN = Cout <= 256 ? Cout : 256;
+  if (tile && tile->bn > 0) {
+    if (!(tile->bn == 64 || tile->bn == 128 || tile->bn == 256) || Cout % tile->bn) {
+      *err = "invalid tile shape (BN)";
+      return false;
+    }
+    BN = tile->bn;
+  }
   const bool split = x_lo && w_lo;
   if (tf32 && split) {
     *err = "tf32 operands have no low parts";
@@ -783,7 +812,8 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   }
   Maps m;
   // 3x3 convs on 128-pixel rows stage one 130-pixel box per kernel row
-  const bool dxr = ks == 3 && W == 128 && BN == 64 && (!geom || (geom->oy == -1 && geom->ox == -1));
+  const bool dxr_ok = ks == 3 && W == 128 && BN == 64 && (!geom || (geom->oy == -1 && geom->ox == -1));
+  const bool dxr = dxr_ok && !(tile && tile->dxr == 0);
   // activations (n, H, W, C); box of kch channels x bw pixels x bh rows
   auto encA = [&](CUtensorMap* mp, const void* ptr, int C, int bw, int bh) {
     cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
@@ -806,7 +836,15 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   };
   // two M tiles per work unit when every window holds an even number of
   // them, except for split 64-channel stages (too large twice over)
-  const int mt = (((int64_t)H * W / BM) % 2 == 0 && !(split && BN == 64) && BN <= 128) ? 2 : 1;
+  const bool mt2_ok = ((int64_t)H * W / BM) % 2 == 0 && !(split && BN == 64) && BN <= 128;
+  int mt = mt2_ok ? 2 : 1;
+  if (tile && tile->mt > 0) {
+    if (tile->mt > 2 || (tile->mt == 2 && !mt2_ok)) {
+      *err = "invalid tile shape (MT)";
+      return false;
+    }
+    mt = tile->mt;
+  }
   const int abw = dxr ? W + 2 : W, abh = dxr ? mt : mt * 128 / W;
   if (!encA(&m.a, x, Cin, abw, abh) || !encB(&m.b, w, Cin, ks * ks)) {
     *err = "tensor map (activations or weights) encode failed";

@@ -224,7 +224,10 @@ int* unet_status(const UNet* u);
 // fuse_groupnorm (IDF_TF32 only): GroupNorm and SiLU inside the tensor-core
 // convolutions' operand path; wait_limit: clock64 cycles a bounded device
 // wait may take (0: about 0.5 s)
-void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit);
+void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit, bool autotune = false);
+// autotuner summary: layer classes tuned, and those whose fastest tile shape
+// differs from the built-in choice
+void unet_autotune_stats(const UNet* u, int* tuned, int* changed);
 void unet_set_prof(UNet* u, Prof* p);
 
 // tcgen05 conv (conv_tc.cu)
@@ -254,6 +257,18 @@ struct TcXf {
   int G = 1, cpg = 1, coff = 0, silu = 0;
 };
 
+// Tile shape of a tensor-core convolution: BN output channels per tile, MT
+// 128-pixel M tiles per work unit, dxr = 1 to stage one 130-pixel box per
+// kernel row (3x3 on 128-pixel rows, BN = 64) or 0 for a box per tap.  Zero
+// / negative fields take the built-in choice; every valid shape gives the
+// same result bit for bit (the K order of each output element is fixed).
+struct TcTile {
+  int bn = 0, mt = 0, dxr = -1;
+};
+// The valid tile shapes of a convolution (for autotuning).
+std::vector<TcTile> conv_tc_tiles(int H, int W, int Cin, int Cout, int ks, bool split, bool xf,
+                                  const TcGeom* geom);
+
 // y (float32 NHWC, Cout) = conv(x) over (tap, Cin) [+ the 1x1 conv of x2
 // over Cin2, folded into the same accumulator] [+ res], x / x2 in bfloat16
 // (with low parts for the compensated split) or tf32-rounded float32.  With
@@ -264,7 +279,8 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
                      float* y, float2* bstats, int n, int H, int W, int Cin, int Cout, int ks, int* status,
                      cudaStream_t st, std::string* err, const void* x2 = nullptr, const void* w2 = nullptr,
                      const void* x2_lo = nullptr, const void* w2_lo = nullptr, int Cin2 = 0, bool tf32 = false,
-                     const TcGeom* geom = nullptr, const TcXf* xf = nullptr, long long wait_limit = 0);
+                     const TcGeom* geom = nullptr, const TcXf* xf = nullptr, long long wait_limit = 0,
+                     const TcTile* tile = nullptr);
 
 // Fused per-window UNet of the 16-channel networks (unet_small.cu): 2
 // levels of 16 channels, 32 x 32 windows, GroupNorm(4), no attention, on

@@ -32,6 +32,9 @@
 #include <type_traits>
 #include <vector>
 
+#include <map>
+#include <tuple>
+
 #include "internal.h"
 
 namespace idf {
@@ -1585,6 +1588,11 @@ struct UNet {
   // BF16 / FP8 E4M3 on a 16-channel network: the fused per-window kernel
   // (unet_small.cu) evaluates the whole UNet; nothing else is allocated
   SmallNet* small = nullptr;
+  // tile-shape autotuner: per (convolution, geometry, batch class) the
+  // fastest valid shape, measured once on the first launch of that class
+  bool autotune = false;
+  std::map<std::tuple<const void*, int, int, int, int>, TcTile> tuned;
+  int tuned_changed = 0;
 };
 
 static bool uses_small(const UNetDesc& d, int precision) {
@@ -1912,9 +1920,14 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
 int unet_max_batch(const UNet* u) { return u->max_batch; }
 int64_t unet_launches(const UNet* u) { return u->launches; }
 int* unet_status(const UNet* u) { return u->status; }
-void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit) {
+void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit, bool autotune) {
   u->fuse_gn = fuse_groupnorm && u->precision == 4;
   u->wait_limit = wait_limit;
+  u->autotune = autotune;
+}
+void unet_autotune_stats(const UNet* u, int* tuned, int* changed) {
+  *tuned = u ? (int)u->tuned.size() : 0;
+  *changed = u ? u->tuned_changed : 0;
 }
 void unet_set_prof(UNet* u, Prof* p) { u->prof = p; }
 
@@ -1954,15 +1967,66 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
     const double ob = (std::is_same<TA, tf32>::value || c.u->split) ? 4.0 : 2.0;
     const double by = c.n * H * W * (ob * (w.cin + (w2 ? w2->cin : 0)) + 4.0 * w.cout * (res ? 2 : 1)) +
                       ob * (w.ks * w.ks * w.cin + (w2 ? w2->cin : 0)) * w.cout;
-    const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
     const bool sp = c.u->split;
     const bool tf = std::is_same<TA, tf32>::value;
     const void* wk = tf ? (const void*)w.wtf : (const void*)w.w16;
     const void* wk2 = w2 ? (tf ? (const void*)w2->wtf : (const void*)w2->w16) : nullptr;
-    const bool ok = conv_tc_forward(x, wk, sp ? x_lo : nullptr, sp ? w.w16lo : nullptr, res, y, bs, c.n, H, W,
-                                    w.cin, w.cout, w.ks, c.u->status, c.st, &e, w2 ? x2 : nullptr, wk2,
-                                    w2 && sp ? x2_lo : nullptr, w2 && sp ? w2->w16lo : nullptr,
-                                    w2 ? w2->cin : 0, tf, geom, xf, c.u->wait_limit);
+    auto launch = [&](const TcTile* t) {
+      return conv_tc_forward(x, wk, sp ? x_lo : nullptr, sp ? w.w16lo : nullptr, res, y, bs, c.n, H, W, w.cin,
+                             w.cout, w.ks, c.u->status, c.st, &e, w2 ? x2 : nullptr, wk2,
+                             w2 && sp ? x2_lo : nullptr, w2 && sp ? w2->w16lo : nullptr, w2 ? w2->cin : 0, tf, geom,
+                             xf, c.u->wait_limit, t);
+    };
+    const TcTile* chosen = nullptr;
+    if (c.u->autotune) {
+      // batch class: full batches, or the power of two below a partial one
+      int cls = c.n >= c.u->max_batch ? 1 << 30 : 1;
+      while (cls < (1 << 30) && cls * 2 <= c.n) cls *= 2;
+      const auto key = std::make_tuple((const void*)&w, H, cls, geom ? (geom->oy + 4 * geom->ox + 16 * geom->out_up) : 99,
+                                       xf ? 1 : 0);
+      auto it = c.u->tuned.find(key);
+      if (it == c.u->tuned.end()) {
+        // time every valid shape (one warm launch, two timed); results are
+        // the same bit for bit, so the launches only rewrite the output
+        const auto cand = conv_tc_tiles(H, W, w.cin, w.cout, w.ks, sp, xf != nullptr, geom);
+        TcTile best{};
+        float best_ms = 1e30f;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        for (const TcTile& t : cand) {
+          if (!launch(&t)) continue;
+          cudaEventRecord(a, c.st);
+          bool ok2 = launch(&t) && launch(&t);
+          cudaEventRecord(b, c.st);
+          if (!ok2 || cudaEventSynchronize(b) != cudaSuccess) continue;
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, a, b);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+          }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaGetLastError();
+        // the built-in choice, for the summary
+        TcTile dflt{};
+        {
+          const int bn0 = w.cout <= 256 ? w.cout : 256;
+          const bool dx0 = w.ks == 3 && W == 128 && bn0 == 64 && (!geom || (geom->oy == -1 && geom->ox == -1));
+          const bool m20 = ((int64_t)H * W / 128) % 2 == 0 && !(sp && bn0 == 64) && bn0 <= 128;
+          dflt.bn = bn0;
+          dflt.mt = m20 ? 2 : 1;
+          dflt.dxr = dx0 ? 1 : 0;
+        }
+        if (best.bn && (best.bn != dflt.bn || best.mt != dflt.mt || best.dxr != dflt.dxr)) c.u->tuned_changed++;
+        it = c.u->tuned.emplace(key, best).first;
+      }
+      if (it->second.bn) chosen = &it->second;
+    }
+    const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
+    const bool ok = launch(chosen);
     if (c.u->prof) c.u->prof->end(pr, c.st);
     if (!ok) {
       c.ok = false;

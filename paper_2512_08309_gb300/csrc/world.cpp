@@ -129,7 +129,8 @@ struct Level {
   int64_t store_reads = 0, store_writes = 0;
   // conditioning vector and embedding (cond_dim > 0), AutoGuidance guide
   std::vector<float> condz;
-  float* d_condE = nullptr;
+  float* d_condE = nullptr;   // the main network's embedding E
+  float* d_condEg = nullptr;  // the guide network's own E
   float* d_condz = nullptr;
   UNet* guide = nullptr;
   float w_guide = 0.0f;
@@ -150,7 +151,7 @@ struct idf_world {
   float* F = nullptr; size_t F_cap = 0;
   float* x_in = nullptr; size_t x_cap = 0;
   float* xs = nullptr; size_t xs_cap = 0;          // window states of multi-step rounds
-  float* bias = nullptr; size_t bias_cap = 0;      // per-window conditioning biases
+  float* bias = nullptr; size_t bias_cap = 0;      // per-window conditioning biases (main, then guide)
   float* Fg = nullptr; size_t Fg_cap = 0;          // guide network outputs
   int32_t* tab = nullptr; size_t tab_cap = 0;
   float* dense = nullptr; size_t dense_cap = 0;    // assembled level results
@@ -522,13 +523,21 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
       W->launches++;
       float* Fb = W->F + (size_t)b0 * H * H;
       const float* bias = nullptr;
+      const float* bias_g = nullptr;
       if (L.d.cond_dim > 0 && L.unet) {
+        // each network embeds y_i with its own E
         const int c0 = L.d.channels[0];
-        if (!grow(W, &W->bias, &W->bias_cap, (size_t)nb * c0, "conditioning biases")) return false;
+        if (!grow(W, &W->bias, &W->bias_cap, (size_t)2 * nb * c0, "conditioning biases")) return false;
         launch_cond_bias(g.win_ij, nb, W->seed, (uint32_t)L.index, L.d_condz, (float)L.d.cond_amp, L.d_condE,
                          L.d.cond_dim, c0, W->bias, st);
         W->launches++;
         bias = W->bias;
+        if (L.guide) {
+          launch_cond_bias(g.win_ij, nb, W->seed, (uint32_t)L.index, L.d_condz, (float)L.d.cond_amp, L.d_condEg,
+                           L.d.cond_dim, c0, W->bias + (size_t)nb * c0, st);
+          W->launches++;
+          bias_g = W->bias + (size_t)nb * c0;
+        }
       }
       for (int i = 0; i < m; ++i) {
         const int j = j0 + i;
@@ -551,7 +560,7 @@ bool run_level(idf_world* W, Level& L, LevelPlan& P, const Dense* cond) {
             // F = F_guide + w (F_main - F_guide)
             if (!grow(W, &W->Fg, &W->Fg_cap, (size_t)nb * H * H, "guide outputs")) return false;
             const int64_t g0 = unet_launches(L.guide);
-            if (!unet_forward(L.guide, W->x_in, nb, W->Fg, st, &e, bias)) {
+            if (!unet_forward(L.guide, W->x_in, nb, W->Fg, st, &e, bias_g)) {
               W->last_error = e.msg;
               W->poisoned = e.code == 3;
               return false;
@@ -1148,7 +1157,8 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
         return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
       }
       unet_set_prof(L.unet, &W->prof);
-      unet_set_options(L.unet, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles);
+      unet_set_options(L.unet, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles,
+                       opts->autotune != 0);
       const idf_level_desc& dsrc = stack->level[i];
       if (dsrc.cond_dim > 0) {
         // the embedding E is the last (channels[0], cond_dim, 1, 1) tensor
@@ -1161,10 +1171,17 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
       }
       if (dsrc.guidance != 0.0) {
         if (!dsrc.guide_weights || dsrc.n_guide_weights != nw) return bail(IDF_EMODEL);
+        if (dsrc.cond_dim > 0) {
+          const size_t ne = (size_t)L.d.channels[0] * dsrc.cond_dim;
+          if (cudaMalloc(&L.d_condEg, ne * 4) != cudaSuccess ||
+              cudaMemcpy(L.d_condEg, dsrc.guide_weights + nw - ne, ne * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(IDF_ENOMEM);
+        }
         L.guide = unet_create(ud, dsrc.guide_weights, opts->precision, batches[i], &e, W->arena, W->arena_bytes);
         if (!L.guide) return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
         unet_set_prof(L.guide, &W->prof);
-        unet_set_options(L.guide, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles);
+        unet_set_options(L.guide, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles,
+                         opts->autotune != 0);
         L.w_guide = (float)dsrc.guidance;
       }
     }
@@ -1192,6 +1209,7 @@ void idf_world_destroy(idf_world* W) {
     unet_destroy(L.unet);
     unet_destroy(L.guide);
     cudaFree(L.d_condE);
+    cudaFree(L.d_condEg);
     cudaFree(L.d_condz);
     cudaFree(L.d_w1);
     cudaFree(L.d_invB1);
@@ -1295,9 +1313,17 @@ idf_status idf_world_stats(const idf_world* Wc, char* buf, size_t len) {
              (long long)L.store_writes);
     s += b;
   }
-  char b[128];
-  snprintf(b, sizeof b, "], \"kernel_launches\": %lld, \"queries\": %lld", (long long)W->launches,
-           (long long)W->queries);
+  int tuned = 0, changed = 0;
+  for (const Level& L : W->lv) {
+    int t = 0, c = 0;
+    unet_autotune_stats(L.unet, &t, &c);
+    tuned += t;
+    changed += c;
+  }
+  char b[256];
+  snprintf(b, sizeof b,
+           "], \"kernel_launches\": %lld, \"queries\": %lld, \"autotune\": {\"tuned\": %d, \"changed\": %d}",
+           (long long)W->launches, (long long)W->queries, tuned, changed);
   s += b;
   static const char* names[PK_COUNT] = {"conv_tc", "conv_simt", "groupnorm", "attention", "resample",
                                         "gather", "test_denoiser", "blend", "assemble", "decode"};
