@@ -64,6 +64,8 @@ def parse():
                    help="second precision timed on the same workload beside the headline ('' = none)")
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
+    p.add_argument("--autotune", type=int, default=1,
+                   help="1: tensor-core tile shapes picked by the library's autotuner during the warm-up")
     p.add_argument("--student", type=int, default=0,
                    help="distillation mode: train the student on N pairs from the plain sampler, judge it")
     p.add_argument("--epochs", type=int, default=4)
@@ -388,7 +390,8 @@ def run_idf(args, rank, world, local):
     st, wts = stack_and_weights()
     q = args.query
     W = idf.World(0, st, wts, precision=args.precision, device=local, profile=True,
-                  workspace_bytes=int(args.workspace_gb * (1 << 30)), cache_bytes=int(args.cache_gb * (1 << 30)))
+                  workspace_bytes=int(args.workspace_gb * (1 << 30)), cache_bytes=int(args.cache_gb * (1 << 30)),
+                  autotune=bool(args.autotune))
     out = torch.empty((q, q), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -495,7 +498,7 @@ def run_idf(args, rank, world, local):
         "data": "synthetic",
         "config": bench_config(q, args.precision, {"coarse": wins[0] / args.steps, "fine": wins[1] / args.steps},
                                world),
-        "gpu_launches": launches, "output_finite": finite,
+        "gpu_launches": launches, "output_finite": finite, "autotune": s1.get("autotune"),
         "roofline": roofline, "hbm_kernels": hbm,
         "kernel_ms": {k: v["ms"] for k, v in prof.items() if v["launches"]},
         "clocks": clk,
@@ -524,7 +527,7 @@ def run_idf(args, rank, world, local):
     if args.also and args.also != args.precision:
         W2 = idf.World(0, st, wts, precision=args.also, device=local, profile=True,
                        workspace_bytes=int(args.workspace_gb * (1 << 30)),
-                       cache_bytes=int(args.cache_gb * (1 << 30)))
+                       cache_bytes=int(args.cache_gb * (1 << 30)), autotune=bool(args.autotune))
 
         def step2(i):
             W2.cache_clear()

@@ -388,6 +388,10 @@ idf_status idf_student_zero_grad(idf_student* s);
  * memory in declaration order; n must equal the parameter count. */
 idf_status idf_student_read(const idf_student* s, int32_t what, float* host_out, size_t n);
 
+/* Replace the student's weights by host_in (n floats, declaration order;
+ * n must equal the parameter count); the AdamW moments are kept. */
+idf_status idf_student_write(idf_student* s, const float* host_in, size_t n);
+
 /* Message of the last failure on this student. */
 const char* idf_student_last_error(const idf_student* s);
 

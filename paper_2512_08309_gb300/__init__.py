@@ -33,7 +33,7 @@ EXPORTS = [
     "idf_model_param_count", "idf_model_param_shape",
     "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo", "idf_laplacian_decode_noalloc",
     "idf_student_create", "idf_student_loss_grad", "idf_student_adamw", "idf_student_zero_grad",
-    "idf_student_read", "idf_student_last_error", "idf_student_destroy",
+    "idf_student_read", "idf_student_write", "idf_student_last_error", "idf_student_destroy",
 ]
 
 
@@ -125,6 +125,7 @@ def lib():
         "idf_student_adamw": ([vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double], i32),
         "idf_student_zero_grad": ([vp], i32),
         "idf_student_read": ([vp, i32, C.POINTER(C.c_float), C.c_size_t], i32),
+        "idf_student_write": ([vp, C.POINTER(C.c_float), C.c_size_t], i32),
         "idf_student_last_error": ([vp], C.c_char_p),
         "idf_student_destroy": ([vp], None),
     }
@@ -431,6 +432,13 @@ class Student:
         self._chk(lib().idf_student_read(self._h, what, out.ctypes.data_as(C.POINTER(C.c_float)), out.size),
                   "idf_student_read")
         return out
+
+    def write(self, weights):
+        """Replace the weights (declaration order) by a host float32 array."""
+        import numpy as np
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self._chk(lib().idf_student_write(self._h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size),
+                  "idf_student_write")
 
     def weights(self):
         return self.read(0)

@@ -687,6 +687,24 @@ idf_status idf_student_zero_grad(idf_student* s) {
   return IDF_OK;
 }
 
+idf_status idf_student_write(idf_student* s, const float* host_in, size_t n) {
+  if (!s || !host_in || n != s->n_params) return IDF_EINVAL;
+  std::vector<float> packed(s->n_params);
+  size_t off = 0;
+  for (const SConv& c : s->convs) {
+    const int taps = c.ks * c.ks;
+    for (int o = 0; o < c.cout; ++o)
+      for (int ci = 0; ci < c.cin; ++ci)
+        for (int t = 0; t < taps; ++t)
+          packed[c.w_off + ((size_t)t * c.cin + ci) * c.cout + o] = host_in[off + ((size_t)o * c.cin + ci) * taps + t];
+    off += c.n;
+  }
+  if (!ck(s, cudaStreamSynchronize(s->st), "sync") ||
+      !ck(s, cudaMemcpy(s->w, packed.data(), s->n_params * 4, cudaMemcpyHostToDevice), "copy"))
+    return IDF_ECUDA;
+  return IDF_OK;
+}
+
 idf_status idf_student_read(const idf_student* sc, int32_t what, float* host_out, size_t n) {
   idf_student* s = const_cast<idf_student*>(sc);
   if (!s || !host_out || (what != 0 && what != 1) || n != s->n_params) return IDF_EINVAL;

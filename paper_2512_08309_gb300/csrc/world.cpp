@@ -294,6 +294,175 @@ struct RectT {
   int64_t ty0, tx0, ty1, tx1;  // inclusive tile range
 };
 
+// Dense form of plan_level for compact requests: the needed tiles of every
+// round, the missing ones and the windows over them are bitmaps over
+// bounding boxes instead of hash sets (a cold 8192^2 query touches about a
+// million windows), visited row by row, i.e. in the sorted order the hash
+// form sorts into, so that the windows, the cache walk (hits touched,
+// misses, LRU order), the allocation and the tables are the same.
+struct DBox {
+  int64_t y0 = 0, x0 = 0, y1 = -1, x1 = -1;
+  int64_t h() const { return y1 - y0 + 1; }
+  int64_t w() const { return x1 - x0 + 1; }
+  int64_t area() const { return h() > 0 && w() > 0 ? h() * w() : 0; }
+  int64_t at(int64_t y, int64_t x) const { return (y - y0) * w() + (x - x0); }
+};
+
+bool plan_level_dense(Level& L, const std::vector<RectT>& rects, bool dry, LevelPlan& P, std::string* err,
+                      TileStore* store) {
+  const int K = L.R, r = L.r;
+  TileCache& C = L.cache;
+  P.steps.assign(K, StepPlan());
+  std::vector<DBox> nb(K + 1);                 // need box of J_k
+  std::vector<std::vector<int32_t>> slot(K + 1);  // per need cell: -2 not needed, -1 missing, else slot
+  std::vector<std::vector<uint64_t>> missing(K + 1);
+  std::vector<DBox> wb(K);                      // window box of round k (windows on J_k)
+  std::vector<std::vector<int32_t>> widx(K);    // per window cell: batch index or -1
+  DBox& b = nb[K];
+  b.y0 = rects[0].ty0; b.x0 = rects[0].tx0; b.y1 = rects[0].ty1; b.x1 = rects[0].tx1;
+  for (auto& R : rects) {
+    b.y0 = std::min(b.y0, R.ty0); b.x0 = std::min(b.x0, R.tx0);
+    b.y1 = std::max(b.y1, R.ty1); b.x1 = std::max(b.x1, R.tx1);
+  }
+  slot[K].assign(b.area(), -2);
+  for (auto& R : rects)
+    for (int64_t ty = R.ty0; ty <= R.ty1; ++ty)
+      for (int64_t tx = R.tx0; tx <= R.tx1; ++tx) slot[K][b.at(ty, tx)] = -1;
+  for (int k = K; k >= 1; --k) {
+    const DBox& B = nb[k];
+    auto& S = slot[k];
+    auto& mk = missing[k];
+    const bool empty = C.map[k].empty();
+    for (int64_t ty = B.y0; ty <= B.y1; ++ty)
+      for (int64_t tx = B.x0; tx <= B.x1; ++tx) {
+        int32_t& c = S[B.at(ty, tx)];
+        if (c == -2) continue;
+        const uint64_t t = tkey((int32_t)ty, (int32_t)tx);
+        if (!empty) {
+          auto it = C.map[k].find(t);
+          if (it != C.map[k].end()) {
+            if (!dry) {
+              C.touch(it->second);
+              C.hits++;
+            }
+            c = it->second;
+            continue;
+          }
+        }
+        if (k == K && store && store_has(store, L.index, (int32_t)ty, (int32_t)tx)) {
+          P.from_store.push_back(t);
+          c = -3;  // filled by the allocation below
+        } else {
+          mk.push_back(t);
+        }
+      }
+    if (!dry) C.misses += (int64_t)mk.size();
+    // windows over the missing tiles: (ty - m, tx - n), m, n < r
+    DBox& W = wb[k - 1];
+    W.y0 = B.y0 - (r - 1); W.x0 = B.x0 - (r - 1); W.y1 = B.y1; W.x1 = B.x1;
+    std::vector<uint8_t> wm(W.area(), 0);
+    for (uint64_t t : mk)
+      for (int m = 0; m < r; ++m)
+        for (int n = 0; n < r; ++n) wm[W.at(khi(t) - m, klo(t) - n)] = 1;
+    StepPlan& sp = P.steps[k - 1];
+    auto& wi = widx[k - 1];
+    wi.assign(W.area(), -1);
+    int32_t nw = 0;
+    for (int64_t i = W.y0; i <= W.y1; ++i)
+      for (int64_t j = W.x0; j <= W.x1; ++j) {
+        if (!wm[W.at(i, j)]) continue;
+        wi[W.at(i, j)] = nw++;
+        sp.win_ij.push_back((int32_t)i);
+        sp.win_ij.push_back((int32_t)j);
+        if (!P.any_windows) {
+          P.wi_min = P.wi_max = i;
+          P.wj_min = P.wj_max = j;
+        }
+        P.any_windows = true;
+        P.wi_min = std::min(P.wi_min, i);
+        P.wi_max = std::max(P.wi_max, i);
+        P.wj_min = std::min(P.wj_min, j);
+        P.wj_max = std::max(P.wj_max, j);
+      }
+    P.n_win_max = std::max(P.n_win_max, (size_t)nw);
+    if (k - 1 >= 1) {
+      DBox& N = nb[k - 1];
+      N.y0 = W.y0; N.x0 = W.x0; N.y1 = W.y1 + (r - 1); N.x1 = W.x1 + (r - 1);
+      auto& Sn = slot[k - 1];
+      Sn.assign(N.area(), -2);
+      for (int64_t i = W.y0; i <= W.y1; ++i)
+        for (int64_t j = W.x0; j <= W.x1; ++j) {
+          if (!wm[W.at(i, j)]) continue;
+          for (int m = 0; m < r; ++m)
+            for (int n = 0; n < r; ++n) Sn[N.at(i + m, j + n)] = -1;
+        }
+    }
+  }
+  if (dry) return true;
+  std::vector<std::pair<int, uint64_t>> inserted;
+  auto rollback = [&]() {
+    for (auto& kt : inserted) {
+      auto it = C.map[kt.first].find(kt.second);
+      const int32_t os = it->second;
+      C.map[kt.first].erase(it);
+      C.unlink(os);
+      C.free_list.push_back(os);
+    }
+    *err = "tile cache too small for this query's working set; raise cache_bytes";
+    P.loads.clear();
+    return false;
+  };
+  for (uint64_t t : P.from_store) {
+    const int32_t sl = C.alloc();
+    if (sl < 0) return rollback();
+    C.insert(K, t, sl);
+    inserted.emplace_back(K, t);
+    P.loads.emplace_back(sl, t);
+    slot[K][nb[K].at(khi(t), klo(t))] = sl;
+  }
+  for (int k = 1; k <= K; ++k)
+    for (uint64_t t : missing[k]) {
+      const int32_t sl = C.alloc();
+      if (sl < 0) return rollback();
+      C.insert(k, t, sl);
+      inserted.emplace_back(k, t);
+      slot[k][nb[k].at(khi(t), klo(t))] = sl;
+    }
+  // tables
+  for (int k = 0; k < K; ++k) {
+    StepPlan& sp = P.steps[k];
+    const size_t nw = sp.win_ij.size() / 2;
+    if (k >= 1) {
+      sp.win_slots.resize(nw * r * r);
+      const DBox& B = nb[k];
+      for (size_t i = 0; i < nw; ++i)
+        for (int m = 0; m < r; ++m)
+          for (int n = 0; n < r; ++n) {
+            const int32_t sl = slot[k][B.at(sp.win_ij[2 * i] + m, sp.win_ij[2 * i + 1] + n)];
+            if (sl < 0) {
+              *err = "internal: input tile missing from the plan";
+              return false;
+            }
+            sp.win_slots[(i * r + m) * r + n] = sl;
+          }
+    }
+    const auto& mt = missing[k + 1];
+    sp.tiles.resize(4 * mt.size());
+    sp.tile_wins.resize(mt.size() * r * r);
+    const DBox& W = wb[k];
+    for (size_t t = 0; t < mt.size(); ++t) {
+      const int32_t ty = khi(mt[t]), tx = klo(mt[t]);
+      sp.tiles[4 * t] = ty;
+      sp.tiles[4 * t + 1] = tx;
+      sp.tiles[4 * t + 2] = k >= 1 ? slot[k][nb[k].at(ty, tx)] : -1;
+      sp.tiles[4 * t + 3] = slot[k + 1][nb[k + 1].at(ty, tx)];
+      for (int m = 0; m < r; ++m)
+        for (int n = 0; n < r; ++n) sp.tile_wins[(t * r + m) * r + n] = widx[k][W.at(ty - m, tx - n)];
+    }
+  }
+  return true;
+}
+
 // Plan (and, unless dry, allocate cache slots for) the query of J_K over the
 // tile rects.  With a persistent store, final-round tiles it holds count as
 // available (read into cache slots instead of computed).  Returns false with
@@ -301,6 +470,19 @@ struct RectT {
 bool plan_level(Level& L, const std::vector<RectT>& rects, bool dry, LevelPlan& P,
                 std::string* err, TileStore* store = nullptr) {
   const int K = L.R, r = L.r;
+  // compact requests (their bounding box at most 4x their area, grown by
+  // the cone, a few million cells at most) take the dense form
+  if (!rects.empty()) {
+    int64_t y0 = rects[0].ty0, x0 = rects[0].tx0, y1 = rects[0].ty1, x1 = rects[0].tx1, area = 0;
+    for (auto& R : rects) {
+      y0 = std::min(y0, R.ty0); x0 = std::min(x0, R.tx0); y1 = std::max(y1, R.ty1); x1 = std::max(x1, R.tx1);
+      area += (R.ty1 - R.ty0 + 1) * (R.tx1 - R.tx0 + 1);
+    }
+    const int64_t g = (int64_t)K * (r - 1);
+    const double box = (double)(y1 - y0 + 1 + 2 * g) * (double)(x1 - x0 + 1 + 2 * g);
+    if ((double)(y1 - y0 + 1) * (x1 - x0 + 1) <= 4.0 * area && box <= 6.4e7)
+      return plan_level_dense(L, rects, dry, P, err, store);
+  }
   TileCache& C = L.cache;
   P.steps.assign(K, StepPlan());
   std::vector<uint64_t> need;

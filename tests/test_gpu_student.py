@@ -139,3 +139,43 @@ def test_distillation_gain_over_untrained_student(idf):
     S.close()
     print(f"held-out loss {before:.4e} -> {after:.4e}")
     assert after < 0.9 * before
+
+
+def test_autograd_function_against_finite_differences(idf):
+    # the loss as a torch.autograd.Function over the library's forward and
+    # backward kernels: its gradient against central finite differences of
+    # the same loss along random directions, and a torch optimiser driving
+    # the library's training step
+    from paper_2512_08309_gb300.autograd import student_loss
+    lv = synth.level(levels=2, channels=(8, 8), in_ch=1, out_ch=1, window=16, gn_groups=4)
+    w0 = _w(lv, 5)
+    x, t = _batch(3, 16, 6)
+    S = idf.Student(lv, w0, max_batch=4)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    w = torch.tensor(w0, requires_grad=True)
+    loss = student_loss(w, xd, td, 0.8, S)
+    loss.backward()
+    g = w.grad.detach().numpy().astype(np.float64)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        v = rng.standard_normal(w0.size)
+        v /= np.linalg.norm(v)
+        h = 1e-2
+        lp = float(student_loss(torch.tensor((w0 + h * v).astype(np.float32)), xd, td, 0.8, S))
+        lm = float(student_loss(torch.tensor((w0 - h * v).astype(np.float32)), xd, td, 0.8, S))
+        fd = (lp - lm) / (2 * h)
+        an = float(g @ v)
+        print(f"directional derivative: autograd {an:.6e}, finite differences {fd:.6e}")
+        assert abs(fd - an) <= 2e-2 * abs(an) + 1e-6
+    # a torch optimiser over the Function lowers the loss
+    w = torch.tensor(w0, requires_grad=True)
+    opt = torch.optim.AdamW([w], lr=2e-3)
+    first = None
+    for _ in range(20):
+        opt.zero_grad()
+        l = student_loss(w, xd, td, 0.8, S)
+        l.backward()
+        opt.step()
+        first = float(l) if first is None else first
+    assert float(student_loss(w, xd, td, 0.8, S)) < first
+    S.close()
