@@ -351,6 +351,54 @@ idf_status idf_laplacian_decode_noalloc(const idf_model_stack* stack, const floa
 idf_status idf_laplacian_halo(const idf_model_stack* stack, int64_t x0, int64_t y0, int32_t w,
                               int32_t h, int64_t L_rect[4], int64_t H_rect[4]);
 
+/* ------------------------------------------------------- voxel volumes */
+
+/* InfiniteDiffusion on Z^3 (the method is defined on S = Z^d, Sec. 3.2;
+ * Alg. 3 computes kappa per dimension): a seeded, lazily evaluated, infinite
+ * voxel volume queried by boxes in any order.  Windows (i, j, l) cover
+ * [i s, i s + window) x [j s, ...) x [l s, ...) in (z, y, x); tiles are
+ * stride^3, cached per blended step with LRU eviction; blending is Eq. 2
+ * with the separable linear weight window cubed; the noise is N3(seed, 0,
+ * step, x, y, z) = Philox4x32-10 with counter (x, y, z, 2^31 + level 2^16 +
+ * step) and this library's Box-Muller (see idf_noise_fill); EDM
+ * preconditioning and the rho-schedule as for a 2-D level.  The denoiser is
+ * F(x) = conv2(silu(gn(conv1(x)))) (3x3x3, zero padding per window, `channels`
+ * <= 8 hidden channels in `groups` GroupNorm groups, window^3 <= 4096,
+ * weights conv1 (channels, 1, 3, 3, 3) then conv2 (1, channels, 3, 3, 3)),
+ * or with test_denoiser 1 / 2 / 3 the constant 0.5 / identity / identity +
+ * u/H - 2 v/H + 3 w/H (window-local z, y, x).  Float32 throughout. */
+typedef struct {
+  int32_t window, stride, steps;
+  double sigma_max, sigma_min, rho, sigma_data, blend_eps;
+  int32_t channels, groups;
+  int32_t test_denoiser;
+  const float* weights;  /* host, copied; NULL for test denoisers */
+  size_t n_weights;
+} idf_volume_desc;
+
+typedef struct idf_volume idf_volume;
+
+/* Create a volume on a device with a tile cache of cache_bytes (0 = 1 GiB).
+ * IDF_EINVAL for an invalid descriptor, IDF_EMODEL for weights that do not
+ * match, IDF_ENOMEM / IDF_ECUDA on device failures. */
+idf_status idf_volume_create(uint64_t seed, const idf_volume_desc* desc, int32_t device, size_t cache_bytes,
+                             idf_volume** out);
+
+/* The result over [x0, x0+w) x [y0, y0+h) x [z0, z0+d) into out_host
+ * (caller-owned, w*h*d floats, out[(z * h + y) * w + x]); blocks until done.
+ * Tile indices must stay within +-2^20; w*h*d <= 2^30. */
+idf_status idf_volume_query(idf_volume* v, int64_t x0, int64_t y0, int64_t z0, int32_t w, int32_t h,
+                            int32_t d, float* out_host);
+
+/* Counters: out[0] windows evaluated, out[1] tiles computed, out[2] cache
+ * hits, out[3] cache misses. */
+idf_status idf_volume_stats(const idf_volume* v, int64_t out[4]);
+
+const char* idf_volume_last_error(const idf_volume* v);
+
+/* NULL-safe. */
+void idf_volume_destroy(idf_volume* v);
+
 /* ------------------------------------------------------ learned student */
 
 /* A student denoiser trained on the GPU by this library's own forward and

@@ -34,6 +34,7 @@ EXPORTS = [
     "idf_unet_forward", "idf_laplacian_decode", "idf_laplacian_halo", "idf_laplacian_decode_noalloc",
     "idf_student_create", "idf_student_loss_grad", "idf_student_adamw", "idf_student_zero_grad",
     "idf_student_read", "idf_student_write", "idf_student_last_error", "idf_student_destroy",
+    "idf_volume_create", "idf_volume_query", "idf_volume_stats", "idf_volume_last_error", "idf_volume_destroy",
 ]
 
 
@@ -74,6 +75,15 @@ class idf_world_opts(C.Structure):
         ("precision", C.c_int32), ("cache_bytes", C.c_size_t), ("device", C.c_int32),
         ("workspace_bytes", C.c_size_t), ("max_batch", C.c_int32), ("profile", C.c_int32),
         ("device_wait_budget_cycles", C.c_uint64), ("autotune", C.c_int32), ("groupnorm_in_conv", C.c_int32),
+    ]
+
+
+class idf_volume_desc(C.Structure):
+    _fields_ = [
+        ("window", C.c_int32), ("stride", C.c_int32), ("steps", C.c_int32),
+        ("sigma_max", C.c_double), ("sigma_min", C.c_double), ("rho", C.c_double), ("sigma_data", C.c_double),
+        ("blend_eps", C.c_double), ("channels", C.c_int32), ("groups", C.c_int32), ("test_denoiser", C.c_int32),
+        ("weights", C.POINTER(C.c_float)), ("n_weights", C.c_size_t),
     ]
 
 
@@ -128,6 +138,11 @@ def lib():
         "idf_student_write": ([vp, C.POINTER(C.c_float), C.c_size_t], i32),
         "idf_student_last_error": ([vp], C.c_char_p),
         "idf_student_destroy": ([vp], None),
+        "idf_volume_create": ([u64, C.POINTER(idf_volume_desc), i32, C.c_size_t, C.POINTER(vp)], i32),
+        "idf_volume_query": ([vp, i64, i64, i64, i32, i32, i32, vp], i32),
+        "idf_volume_stats": ([vp, C.POINTER(i64)], i32),
+        "idf_volume_last_error": ([vp], C.c_char_p),
+        "idf_volume_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -449,6 +464,54 @@ class Student:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().idf_student_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Volume:
+    """idf_volume: a seeded infinite voxel volume (sampling on Z^3)."""
+
+    def __init__(self, seed: int, desc: dict, weights=None, device: int = 0, cache_bytes: int = 0):
+        import numpy as np
+        self._keep = _Keep()
+        d = idf_volume_desc()
+        for k in ("window", "stride", "steps", "channels", "groups", "test_denoiser"):
+            setattr(d, k, int(desc.get(k, 0)))
+        for k in ("sigma_max", "sigma_min", "rho", "sigma_data", "blend_eps"):
+            setattr(d, k, float(desc[k]))
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            self._keep.refs.append(w)
+            d.weights = w.ctypes.data_as(C.POINTER(C.c_float))
+            d.n_weights = w.size
+        h = C.c_void_p()
+        st = lib().idf_volume_create(C.c_uint64(seed), C.byref(d), device, cache_bytes, C.byref(h))
+        if st != IDF_OK:
+            raise IdfError(st, "idf_volume_create")
+        self._h = h
+
+    def query(self, x0: int, y0: int, z0: int, w: int, h: int, d: int):
+        import numpy as np
+        out = np.empty((d, h, w), dtype=np.float32)
+        st = lib().idf_volume_query(self._h, x0, y0, z0, w, h, d, out.ctypes.data_as(C.c_void_p))
+        if st != IDF_OK:
+            m = lib().idf_volume_last_error(self._h)
+            raise IdfError(st, f"idf_volume_query: {m.decode() if m else ''}")
+        return out
+
+    def stats(self) -> dict:
+        a = (C.c_int64 * 4)()
+        _check(lib().idf_volume_stats(self._h, a), "idf_volume_stats")
+        return {"windows_evaluated": a[0], "tiles_computed": a[1], "cache_hits": a[2], "cache_misses": a[3]}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().idf_volume_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

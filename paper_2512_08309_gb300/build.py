@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libidf.so")
 SOURCES = ["world.cpp", "store.cpp", "sampler_kernels.cu", "unet.cu", "unet_small.cu", "conv_tc.cu",
-           "decode_noalloc.cu", "student.cu"]
+           "decode_noalloc.cu", "student.cu", "volume.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -229,3 +229,21 @@ def fbm_lowband(n: int = 2048, beta: float = 2.2, seed: int = 0,
     fmin, fmax = field.min(), field.max()
     field = lo_s + (field - fmin) * (hi_s - lo_s) / (fmax - fmin)
     return field.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Voxel volumes (sampling on Z^3)
+# ---------------------------------------------------------------------------
+
+def volume_desc(test_denoiser: int = 0, channels: int = 8, window: int = 16, stride: int = 8,
+                steps: int = 3) -> dict:
+    """A volume level: 16^3 windows at stride 8, 3 steps from 80 to 0.02, and
+    (test_denoiser 0) the small 3-D network of 8 hidden channels, GroupNorm(4)."""
+    return dict(window=window, stride=stride, steps=steps, sigma_max=80.0, sigma_min=0.02, rho=7.0,
+                sigma_data=0.5, blend_eps=1e-3, channels=channels, groups=4, test_denoiser=test_denoiser)
+
+
+def volume_weights(desc: dict, weight_seed: int = 0) -> np.ndarray:
+    """Weights of the 3-D network (conv1 (C, 1, 3, 3, 3), conv2 (1, C, 3, 3, 3))."""
+    C = int(desc["channels"])
+    return weights([(C, 1, 3, 3, 3), (1, C, 3, 3, 3)], weight_seed, 100)

@@ -30,7 +30,7 @@ def test_header_symbols_exported():
     idf = _lib()
     L = idf.lib()
     syms = header_symbols()
-    assert len(syms) == 28
+    assert len(syms) == 33
     for s in syms:
         assert hasattr(L, s), s
     assert sorted(idf.EXPORTS) == syms
