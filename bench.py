@@ -80,6 +80,9 @@ def parse():
                         "tensor-core kernel; fp32: the plain sampler)")
     p.add_argument("--profile-unet", type=int, default=0,
                    help="profiling mode: one warm-up and one timed fine-level UNet forward on N windows")
+    p.add_argument("--profile-small", type=int, default=0,
+                   help="profiling mode: two forwards of the fused 16-channel UNet on N 32x32 windows "
+                        "(--small-precision)")
     p.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                    help="where the nvidia-smi clock samples of the timed region are written")
     p.add_argument("--no-e2e", action="store_true")
@@ -625,6 +628,34 @@ def run_profile_unet(args):
     return 0
 
 
+def run_profile_small(args):
+    """Small-footprint profiling case of the fused 16-channel kernel: the
+    single-level network on N 32x32 windows, two forwards (one launch each),
+    timed with CUDA events."""
+    import torch
+
+    import paper_2512_08309_gb300 as idf
+    import synth
+    st = synth.config1_stack()
+    wts = [synth.weights(idf.param_shapes(lv), 0, i) for i, lv in enumerate(st["level"])]
+    n = args.profile_small
+    W = idf.World(0, st, wts, precision=args.small_precision, max_batch=n, cache_bytes=64 << 20)
+    x = torch.randn((n, 1, 32, 32), device="cuda")
+    y = torch.empty((n, 1, 32, 32), device="cuda")
+    W.unet_forward(0, x.data_ptr(), n, y.data_ptr())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    W.unet_forward(0, x.data_ptr(), n, y.data_ptr())
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    print(json.dumps({"profile_small": n, "precision": args.small_precision, "ms": ms,
+                      "windows_per_s": n / (ms / 1000.0), "finite": bool(torch.isfinite(y).all().item())}))
+    W.close()
+    return 0
+
+
 def run_student(args):
     """Distil the half-width 2-step student from the plain sampler.
 
@@ -920,6 +951,8 @@ def main():
         return run_student(args)
     if args.profile_unet:
         return run_profile_unet(args)
+    if args.profile_small:
+        return run_profile_small(args)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)

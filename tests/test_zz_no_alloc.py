@@ -60,3 +60,31 @@ def test_noalloc_decode_rejects_queries_beyond_its_scratch():
         idf.laplacian_decode_noalloc(st, L.data_ptr(), Lr, Lr[2], H.data_ptr(), Hr, Hr[2], x0, y0, w, h,
                                      out.data_ptr(), w)
     assert e.value.status == idf.IDF_EINVAL
+
+
+def test_noalloc_decode_matches_the_oracle_decode():
+    # directly against the FP64 oracle's decode of the same bands (its
+    # device-computed blur taps may differ from the host's in the last bit)
+    import paper_2512_08309_gb300 as idf
+    from oracle import laplacian as OL
+    idf.lib()
+    st = synth.config2_stack()
+    x0, y0, w, h = -301, 77, 200, 150
+    Lr, Hr, L, H = _bands(idf, st, x0, y0, w, h, seed=7)
+    got = torch.full((h, w), float("nan"), device="cuda")
+    idf.laplacian_decode_noalloc(st, L.data_ptr(), Lr, Lr[2], H.data_ptr(), Hr, Hr[2], x0, y0, w, h,
+                                 got.data_ptr(), w)
+    torch.cuda.synchronize()
+    Ln, Hn = L.cpu().numpy().astype(np.float64), H.cpu().numpy().astype(np.float64)
+
+    def lfun(cy0, cx0, ch, cw):
+        return Ln[cy0 - Lr[1]:cy0 - Lr[1] + ch, cx0 - Lr[0]:cx0 - Lr[0] + cw]
+
+    def hfun(yy0, xx0, hh, ww):
+        return Hn[yy0 - Hr[1]:yy0 - Hr[1] + hh, xx0 - Hr[0]:xx0 - Hr[0] + ww]
+
+    ref = OL.decode_metres(lfun, hfun, y0, x0, h, w, factor=st["lap_factor"], blur_sigma=st["lap_blur_sigma"],
+                           radius=st["lap_radius"], low_mu=st["low_mu"], low_scale=st["low_scale"],
+                           res_scale=st["res_scale"])
+    g = got.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g - ref)) <= 1e-5 * np.max(np.abs(ref))
