@@ -64,6 +64,10 @@ def parse():
                    help="second precision timed on the same workload beside the headline ('' = none)")
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
+    p.add_argument("--pairs", type=int, default=0,
+                   help="1: tensor-core convolutions on CTA pairs (cta_group::2) where the shape allows")
+    p.add_argument("--graphs", type=int, default=1,
+                   help="1: the end-to-end leg replays repeated UNet forwards as CUDA graphs")
     p.add_argument("--autotune", type=int, default=1,
                    help="1: tensor-core tile shapes picked by the library's autotuner during the warm-up")
     p.add_argument("--student", type=int, default=0,
@@ -394,7 +398,7 @@ def run_idf(args, rank, world, local):
     q = args.query
     W = idf.World(0, st, wts, precision=args.precision, device=local, profile=True,
                   workspace_bytes=int(args.workspace_gb * (1 << 30)), cache_bytes=int(args.cache_gb * (1 << 30)),
-                  autotune=bool(args.autotune))
+                  autotune=bool(args.autotune), cta_pairs=bool(args.pairs))
     out = torch.empty((q, q), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -469,6 +473,29 @@ def run_idf(args, rank, world, local):
                 else None,
                 "avg_launch_ms": tc["ms"] / max(1, tc["launches"]),
                 "share_of_step": tc["ms"] / ms if ms > 0 else None}
+    # per-launch roofline of the convolutions: each launch shape's attainable
+    # time is max(FLOPs x MMA work factor / tensor peak, algorithmic bytes /
+    # HBM peak) (the 64-channel layers at 128^2 move more bytes per FLOP
+    # than the machine balance, so the HBM bounds them); the fraction is the
+    # attainable time over the measured time, summed over the timed launches
+    d0 = {(a, b): (n, t) for a, b, n, t in s0.get("conv_tc_shapes", [])}
+    att = meas = hbm_t = 0.0
+    for a, b, n, t in s1.get("conv_tc_shapes", []):
+        n0, t0 = d0.get((a, b), (0, 0.0))
+        if n - n0 <= 0:
+            continue
+        tt = a * mma_factor / (peak * 1e12)
+        tb = b / (pk["hbm_gbs"] * 1e9)
+        att += (n - n0) * max(tt, tb)
+        hbm_t += (n - n0) * max(tt, tb) if tb > tt else 0.0
+        meas += (t - t0) / 1000.0
+    if meas > 0:
+        roofline["per_launch"] = {
+            "frac_of_attainable": att / meas, "attainable_ms": att * 1000.0, "measured_ms": meas * 1000.0,
+            "hbm_bound_share_of_attainable": hbm_t / att if att > 0 else None,
+            "tensor_peak_tflops": peak, "hbm_peak_gbs": pk["hbm_gbs"],
+            "rule": "sum over launches of max(FLOPs x MMA factor / tensor peak, algorithmic bytes / HBM peak) "
+                    "/ measured time"}
     hbm = {}
     for k in ("blend", "decode", "groupnorm", "gather"):
         p = prof[k]
@@ -507,30 +534,45 @@ def run_idf(args, rank, world, local):
         "clocks": clk,
     }
 
-    # end to end through the public host-buffer call (D2H inside the timed region)
+    line["error_vs_oracle"] = crop_error(idf, W) if rank == 0 else None
+    W.close()
+
+    # end to end through the public host-buffer call (D2H inside the timed
+    # region), in the configuration a user runs: no per-kernel profiling, so
+    # the UNet forwards repeated across batches and rounds replay as CUDA
+    # graphs
     if not args.no_e2e:
+        We = idf.World(0, st, wts, precision=args.precision, device=local, cuda_graphs=bool(args.graphs),
+                       workspace_bytes=int(args.workspace_gb * (1 << 30)),
+                       cache_bytes=int(args.cache_gb * (1 << 30)), autotune=bool(args.autotune), cta_pairs=bool(args.pairs))
         host = np.empty((q, q), dtype=np.float32)
-        W.cache_clear()
+        We.query(*loc(999), q, q, kind=idf.IDF_OUT_METRES, out=host)   # warm-up (tunes, captures)
         torch.cuda.synchronize()
+        g0 = We.stats()
         barrier(world)
         t0 = time.perf_counter()
         n_e2e = max(1, args.steps)
         for i in range(n_e2e):
-            W.cache_clear()
+            We.cache_clear()
             x0, y0 = loc(1000 + i)
-            W.query(x0, y0, q, q, kind=idf.IDF_OUT_METRES, out=host)
+            We.query(x0, y0, q, q, kind=idf.IDF_OUT_METRES, out=host)
         dt = max_over_ranks(time.perf_counter() - t0, world)
+        g1 = We.stats()
+        We.close()
+        kl = g1["kernel_launches"] - g0["kernel_launches"]
+        hc = g1["graphs"]["host_launch_calls"] - g0["graphs"]["host_launch_calls"]
         line["e2e"] = {"value": world * q * q * n_e2e / dt, "unit": "px/s", "h2d_bytes_per_step": 0,
-                       "d2h_bytes_per_step": q * q * 4, "steps": n_e2e}
-    line["error_vs_oracle"] = crop_error(idf, W) if rank == 0 else None
-    W.close()
+                       "d2h_bytes_per_step": q * q * 4, "steps": n_e2e, "warmup": 1,
+                       "cuda_graphs": bool(args.graphs),
+                       "kernels_per_step": kl / n_e2e, "host_launch_calls_per_step": hc / n_e2e,
+                       "graph_replays_per_step": (g1["graphs"]["replays"] - g0["graphs"]["replays"]) / n_e2e}
 
     # a second precision (by default the compensated three-product bf16
     # path) on the same workload, timed the same way, beside the headline
     if args.also and args.also != args.precision:
         W2 = idf.World(0, st, wts, precision=args.also, device=local, profile=True,
                        workspace_bytes=int(args.workspace_gb * (1 << 30)),
-                       cache_bytes=int(args.cache_gb * (1 << 30)), autotune=bool(args.autotune))
+                       cache_bytes=int(args.cache_gb * (1 << 30)), autotune=bool(args.autotune), cta_pairs=bool(args.pairs))
 
         def step2(i):
             W2.cache_clear()
@@ -611,7 +653,8 @@ def run_profile_unet(args):
     import paper_2512_08309_gb300 as idf
     st, wts = stack_and_weights()
     n = args.profile_unet
-    W = idf.World(0, st, wts, precision=args.precision, max_batch=n, cache_bytes=64 << 20, profile=True)
+    W = idf.World(0, st, wts, precision=args.precision, max_batch=n, cache_bytes=64 << 20, profile=True,
+                  cta_pairs=bool(args.pairs))
     x = torch.randn((n, 2, 128, 128), device="cuda")
     y = torch.empty((n, 1, 128, 128), device="cuda")
     W.unet_forward(1, x.data_ptr(), n, y.data_ptr())
@@ -622,8 +665,9 @@ def run_profile_unet(args):
     s1 = W.stats()
     prof = {k: {f: s1["profile"][k][f] - s0["profile"][k][f] for f in ("launches", "ms", "flops")}
             for k in s1["profile"] if s1["profile"][k]["launches"] - s0["profile"][k]["launches"]}
-    print(json.dumps({"profile_unet": n, "precision": args.precision, "kernels": prof,
-                      "finite": bool(torch.isfinite(y).all().item())}))
+    print(json.dumps({"profile_unet": n, "precision": args.precision, "cta_pairs": bool(args.pairs), "kernels": prof,
+                      "finite": bool(torch.isfinite(y).all().item()), "device_status": s1["device_status"],
+                      "cta_pair_clusters": s1.get("cta_pair_clusters")}))
     W.close()
     return 0
 
@@ -651,7 +695,8 @@ def run_profile_small(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     print(json.dumps({"profile_small": n, "precision": args.small_precision, "ms": ms,
-                      "windows_per_s": n / (ms / 1000.0), "finite": bool(torch.isfinite(y).all().item())}))
+                      "windows_per_s": n / (ms / 1000.0), "finite": bool(torch.isfinite(y).all().item()),
+                      "device_status": W.stats()["device_status"]}))
     W.close()
     return 0
 

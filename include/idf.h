@@ -181,6 +181,16 @@ typedef struct {
                                        tensor-core convolutions' operand path (no normalised
                                        operand in memory); 0 (default) runs them as separate
                                        passes, which is faster here.  Same results bit for bit */
+  int32_t cuda_graphs;              /* 1: a UNet forward repeated with the same batch buffers and
+                                       size (every full batch of a round, every round) is
+                                       captured once as a CUDA graph and then replayed with one
+                                       launch call; same kernels and arguments, same results bit
+                                       for bit.  Off while profile is on.  0 = eager launches */
+  int32_t cta_pairs;                /* 1: the tensor-core convolutions of plain BF16 / TF32 run on
+                                       clusters of two CTAs (cta_group::2: M = 256 products,
+                                       each CTA staging its own pixels and half of the weight
+                                       tile) wherever the shape allows; same products per
+                                       output element.  0 = one CTA per tile */
 } idf_world_opts;
 
 typedef struct {
@@ -306,7 +316,11 @@ idf_status idf_model_param_shape(const idf_level_desc* level, int32_t index, int
 
 /* Phi's network F (Sec. 5.3, the UNet of a level) on a batch of windows:
  * x_dev (n, in_ch, window, window) float32 NCHW, y_dev (n, out_ch, window,
- * window) float32, both device.  Runs in the world's precision. */
+ * window) float32, both device.  Runs in the world's precision, ordered on
+ * cuda_stream and asynchronous: a bounded device-side wait that ran out
+ * during it is not returned here but shows in idf_world_stats
+ * ("device_status") and makes the world's next query fail with
+ * IDF_ETIMEOUT. */
 idf_status idf_unet_forward(idf_world* world, int32_t level, const float* x_dev, int32_t n,
                             float* y_dev, void* cuda_stream);
 

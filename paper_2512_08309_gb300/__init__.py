@@ -75,6 +75,7 @@ class idf_world_opts(C.Structure):
         ("precision", C.c_int32), ("cache_bytes", C.c_size_t), ("device", C.c_int32),
         ("workspace_bytes", C.c_size_t), ("max_batch", C.c_int32), ("profile", C.c_int32),
         ("device_wait_budget_cycles", C.c_uint64), ("autotune", C.c_int32), ("groupnorm_in_conv", C.c_int32),
+        ("cuda_graphs", C.c_int32), ("cta_pairs", C.c_int32),
     ]
 
 
@@ -267,7 +268,8 @@ class World:
                  precision: str = "fp32", cache_bytes: int = 0, device: int = 0,
                  workspace_bytes: int = 0, max_batch: int = 0, profile: bool = False,
                  wait_budget_cycles: int = 0, groupnorm_in_conv: bool = False,
-                 guide_weights: Optional[Sequence] = None, autotune: bool = False):
+                 guide_weights: Optional[Sequence] = None, autotune: bool = False,
+                 cuda_graphs: bool = True, cta_pairs: bool = False):
         L = lib()
         self._keep = _Keep()
         self.stack = stack
@@ -279,6 +281,8 @@ class World:
         o.device_wait_budget_cycles = int(wait_budget_cycles)
         o.groupnorm_in_conv = 1 if groupnorm_in_conv else 0
         o.autotune = 1 if autotune else 0
+        o.cuda_graphs = 1 if cuda_graphs else 0
+        o.cta_pairs = 1 if cta_pairs else 0
         h = C.c_void_p()
         _check(L.idf_world_create(C.c_uint64(seed), C.byref(st), C.byref(o), C.byref(h)), "idf_world_create")
         self._h = h
@@ -335,9 +339,15 @@ class World:
         _check(lib().idf_world_cache_clear(self._h), "idf_world_cache_clear", self._h)
 
     def stats(self) -> dict:
-        buf = C.create_string_buffer(1 << 16)
-        _check(lib().idf_world_stats(self._h, buf, len(buf)), "idf_world_stats", self._h)
-        return json.loads(buf.value.decode())
+        n = 1 << 16
+        while True:
+            buf = C.create_string_buffer(n)
+            r = lib().idf_world_stats(self._h, buf, len(buf))
+            if r == IDF_EINVAL and n < (1 << 26):
+                n *= 4   # the summary did not fit
+                continue
+            _check(r, "idf_world_stats", self._h)
+            return json.loads(buf.value.decode())
 
     def last_error(self) -> str:
         m = lib().idf_world_last_error(self._h)

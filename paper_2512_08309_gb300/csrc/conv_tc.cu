@@ -99,11 +99,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// The same with acquire at cluster scope: for barriers that the other CTA of
+// a pair arrives on (remote arrivals, multicast commits).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait.  honour_abort: give up as soon as another role aborted.
+// CL: acquire at cluster scope.
+template <bool CL = false>
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                          int* status, bool honour_abort, long long limit) {
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!(CL ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))) {
     if (honour_abort && *abort_flag) return false;
     if (clock64() - t0 > limit) {
       atomicExch(status, 1);
@@ -120,6 +136,27 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// CTA-pair forms: the copy lands in this CTA's shared memory and completes
+// its bytes on the barrier at cluster address bar_cl, which may be the even
+// CTA's (one barrier per stage counts both CTAs' copies).
+__device__ __forceinline__ void tma_load_4d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cl, int c0,
+                                                 int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(bar_cl), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cl, int c0,
+                                                 int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(bar_cl), "r"(c0), "r"(c1)
       : "memory");
 }
 
@@ -183,6 +220,63 @@ __device__ __forceinline__ void mma_step(uint32_t tmem_d, uint64_t adesc, uint64
                                          uint32_t accumulate) {
   if (TF32) mma_tf32(tmem_d, adesc, bdesc, idesc, accumulate);
   else mma_bf16(tmem_d, adesc, bdesc, idesc, accumulate);
+}
+
+// CTA-pair (cta_group::2) forms: one thread of the even CTA of a cluster
+// pair issues M = 256 products whose rows 0-127 come from its own shared
+// memory and rows 128-255 from its peer's (the same offsets), whose B columns
+// are split between the two (the first BN / 2 rows of the weight tile in the
+// even CTA, the rest in the odd one), and whose accumulator tile lives at
+// the same tensor-memory address in both CTAs, each holding its own 128 rows.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives once on the barrier at this offset in both CTAs of the pair when
+// every product this thread issued before it has completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((unsigned short)3)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Address of the same shared-memory object in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -270,7 +364,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // the activations in L2.  The shared-memory ring of STAGES stages runs
 // across unit boundaries; two TMEM accumulator sets (2 x MT x BN columns)
 // let the epilogue of one unit overlap the main loop of the next.
-template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF>
+//
+// PAIR (clusters of two CTAs on one TPC, cta_group::2): a unit is 2 MT M
+// tiles, MT of them in each CTA, times one BN-channel N tile.  Each CTA
+// stages its own pixels and half of the weight tile (BN / 2 rows), so a
+// stage carries a third fewer bytes per product; the even CTA's MMA thread
+// issues M = 256 products over both CTAs' stages once a stage's copies have
+// landed in both (they complete their bytes on one barrier of the even CTA,
+// which expects those of both), and its commits arrive on both CTAs'
+// barriers.  Both
+// epilogues read their own accumulator rows and release the accumulator with
+// arrivals on the even CTA's barrier.  The arithmetic per output element is
+// that of the single-CTA kernel.
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF, bool PAIR = false>
 __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmA_lo,
@@ -284,10 +390,12 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
   // 130-pixel activation box per image row (halo columns zero-filled; MT
   // rows in one box) read by the three horizontal taps at row offsets 0, 1,
   // 2, and the three taps' weights.
+  static_assert(!PAIR || (!SPLIT && !XF), "the CTA-pair kernels take plain bf16 / tf32 operands");
   constexpr int A_ROW = DXR ? (BM + 2) * 128 : BM * 128;    // bytes of one M tile's rows
   constexpr int A_BOX = A_ROW * MT;                         // bytes TMA writes
   constexpr int A_BYTES = (A_BOX + 1023) / 1024 * 1024;     // region, 1024-aligned
-  constexpr int B_BYTES = BN * 128;
+  constexpr int BNL = PAIR ? BN / 2 : BN;                   // weight rows staged by this CTA
+  constexpr int B_BYTES = BNL * 128;
   constexpr int NB = DXR ? 3 : 1;                           // weight tiles per stage
   constexpr int NP = SPLIT ? 2 : 1;                         // hi (and lo) parts per operand
   constexpr int STAGE_BYTES = NP * (A_BYTES + NB * B_BYTES);
@@ -306,15 +414,26 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
   __shared__ int skip_sh;
   uint8_t* smem = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
   volatile int* abort_flag = &abort_sh;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;  // PAIR: 0 = the MMA-issuing CTA
   // once any CTA of any launch has given up on a wait, later CTAs return at
-  // once (one thread reads the status so that the whole CTA decides alike)
-  if (threadIdx.x == 0) skip_sh = *(volatile int*)p.status;
-  __syncthreads();
-  if (skip_sh) return;
+  // once (one thread reads the status so that the whole CTA decides alike;
+  // for a pair, the even CTA decides for both, after the cluster sync below)
+  if (!PAIR) {
+    if (threadIdx.x == 0) skip_sh = *(volatile int*)p.status;
+    __syncthreads();
+    if (skip_sh) return;
+  }
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t HW = (int64_t)p.H * p.W;
-  const int n_units = p.m_tiles / MT * p.n_tiles;
+  constexpr int MU = PAIR ? 2 * MT : MT;  // M tiles per unit
+  int n_units = p.m_tiles / MU * p.n_tiles;
+  const int cta0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // this CTA's (pair's) first unit
+  const int ncta = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;   // unit stride
+  // first pixel of unit u's rows in this CTA
+  auto unit_m0 = [&](int u) -> int64_t {
+    return (int64_t)(u / p.n_tiles) * (BM * MU) + (int64_t)rank * (BM * MT);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -324,7 +443,7 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
-      mbar_init(&acce_bar[b], 128);
+      mbar_init(&acce_bar[b], PAIR ? 256 : 128);  // PAIR: both CTAs' epilogue threads
     }
     mbar_init(&drain_bar, 1);
     abort_sh = 0;
@@ -347,32 +466,73 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
     }
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base_sh)),
-                 "r"(2 * ACC_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (PAIR) {
+      // allocated by one warp of each CTA of the pair together
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(&tmem_base_sh)),
+                   "r"(2 * ACC_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(&tmem_base_sh)),
+                   "r"(2 * ACC_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
-  fence_before();
-  __syncthreads();
-  fence_after();
+  if (PAIR) {
+    // both CTAs have started and their barriers exist before either touches
+    // the other's shared memory; then the even CTA's view of the status word
+    // decides for both
+    fence_before();
+    cluster_sync();
+    fence_after();
+    if (rank == 0 && threadIdx.x == 0) {
+      const int v = *(volatile int*)p.status;
+      skip_sh = v;
+      asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_addr(&skip_sh, 1)), "r"(v) : "memory");
+    }
+    cluster_sync();
+    if (skip_sh) n_units = 0;
+  } else {
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
   const uint32_t tmem = tmem_base_sh;
 
   if (warp == 0) {
     if (lane == 0) {
       int last_issue[STAGES];
       for (int s = 0; s < STAGES; ++s) last_issue[s] = -1;
+      // PAIR: both CTAs' copies of a stage complete on the even CTA's
+      // barrier, which expects the bytes of both
+      const uint32_t fb0 = PAIR ? peer_addr(&full_bar[0], 0) : 0u;
+      auto expect = [&](int s, uint32_t bytes) {
+        if (!PAIR) mbar_expect_tx(&full_bar[s], bytes);
+        else if (rank == 0) mbar_expect_tx(&full_bar[s], 2u * bytes);
+      };
+      auto ld4 = [&](void* dst, const CUtensorMap* map, int s, int c0, int c1, int c2, int c3) {
+        if (PAIR) tma_load_4d_pair(dst, map, fb0 + 8u * (uint32_t)s, c0, c1, c2, c3);
+        else tma_load_4d(dst, map, &full_bar[s], c0, c1, c2, c3);
+      };
+      auto ld2 = [&](void* dst, const CUtensorMap* map, int s, int c0, int c1) {
+        if (PAIR) tma_load_2d_pair(dst, map, fb0 + 8u * (uint32_t)s, c0, c1);
+        else tma_load_2d(dst, map, &full_bar[s], c0, c1);
+      };
       uint32_t it = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-        const int64_t m0 = (int64_t)(u / p.n_tiles) * (BM * MT);
-        const int n0 = (u % p.n_tiles) * BN;
+      for (int u = cta0; u < n_units && ok; u += ncta) {
+        const int64_t m0 = unit_m0(u);
+        // this CTA's weight rows: all BN, or its half of them (PAIR)
+        const int n0 = (u % p.n_tiles) * BN + (int)rank * BNL;
         const int win = (int)(m0 / HW);
         const int y0 = (int)((m0 % HW) / p.W);
         for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
-          if (!wait_bar(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true, p.wait_limit)) {
+          if (!wait_bar<PAIR>(&empty_bar[s], ph ^ 1u, abort_flag, p.status, true, p.wait_limit)) {
             ok = false;
             break;
           }
@@ -381,65 +541,84 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
           if (kk >= p.n_iter1) {
             // folded 1x1 operand: the unit's own pixels, kch channels
             const int kc = kk - p.n_iter1;
-            mbar_expect_tx(&full_bar[s], TX2_BYTES);
-            tma_load_4d(a, &tmA2, &full_bar[s], kc * p.kch, 0, y0, win);
-            tma_load_2d(b, &tmB2, &full_bar[s], kc * p.kch, n0);
+            expect(s, TX2_BYTES);
+            ld4(a, &tmA2, s, kc * p.kch, 0, y0, win);
+            ld2(b, &tmB2, s, kc * p.kch, n0);
             if (SPLIT) {
-              tma_load_4d(a + A_BYTES, &tmA2_lo, &full_bar[s], kc * p.kch, 0, y0, win);
-              tma_load_2d(b + NB * B_BYTES, &tmB2_lo, &full_bar[s], kc * p.kch, n0);
+              ld4(a + A_BYTES, &tmA2_lo, s, kc * p.kch, 0, y0, win);
+              ld2(b + NB * B_BYTES, &tmB2_lo, s, kc * p.kch, n0);
             }
           } else if (DXR) {
-            mbar_expect_tx(&full_bar[s], TX_BYTES);
+            expect(s, TX_BYTES);
             const int dyi = kk / p.n_kc, kc = kk % p.n_kc;
-            tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, p.ox, y0 + dyi + p.oy, win);
-            if (SPLIT) tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * p.kch, p.ox, y0 + dyi + p.oy, win);
+            ld4(a, &tmA, s, kc * p.kch, p.ox, y0 + dyi + p.oy, win);
+            if (SPLIT) ld4(a + A_BYTES, &tmA_lo, s, kc * p.kch, p.ox, y0 + dyi + p.oy, win);
             for (int t = 0; t < 3; ++t) {
-              tma_load_2d(b + t * B_BYTES, &tmB, &full_bar[s], kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
-              if (SPLIT)
-                tma_load_2d(b + (3 + t) * B_BYTES, &tmB_lo, &full_bar[s], kc * p.kch,
-                            (dyi * 3 + t) * p.Cout + n0);
+              ld2(b + t * B_BYTES, &tmB, s, kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
+              if (SPLIT) ld2(b + (3 + t) * B_BYTES, &tmB_lo, s, kc * p.kch, (dyi * 3 + t) * p.Cout + n0);
             }
           } else {
-            mbar_expect_tx(&full_bar[s], TX_BYTES);
+            expect(s, TX_BYTES);
             const int tap = kk / p.n_kc, kc = kk % p.n_kc;
             const int dy = tap / p.ks + p.oy, dx = tap % p.ks + p.ox;
-            tma_load_4d(a, &tmA, &full_bar[s], kc * p.kch, dx, y0 + dy, win);
-            tma_load_2d(b, &tmB, &full_bar[s], kc * p.kch, tap * p.Cout + n0);
+            ld4(a, &tmA, s, kc * p.kch, dx, y0 + dy, win);
+            ld2(b, &tmB, s, kc * p.kch, tap * p.Cout + n0);
             if (SPLIT) {
-              tma_load_4d(a + A_BYTES, &tmA_lo, &full_bar[s], kc * p.kch, dx, y0 + dy, win);
-              tma_load_2d(b + B_BYTES, &tmB_lo, &full_bar[s], kc * p.kch, tap * p.Cout + n0);
+              ld4(a + A_BYTES, &tmA_lo, s, kc * p.kch, dx, y0 + dy, win);
+              ld2(b + B_BYTES, &tmB_lo, s, kc * p.kch, tap * p.Cout + n0);
             }
           }
           last_issue[s] = (int)it;
         }
       }
       if (*abort_flag) {
-        // drain the copies this thread issued before leaving
-        for (int s = 0; s < STAGES; ++s)
-          if (last_issue[s] >= 0)
-            wait_bar(&full_bar[s], (uint32_t)(last_issue[s] / STAGES) & 1u, abort_flag, p.status, false, p.wait_limit);
+        if (PAIR && rank == 1) {
+          // this CTA's copies complete on the even CTA's barriers: give the
+          // ones in flight a fixed 100k cycles (tens of microseconds) to land
+          const long long t0 = clock64();
+          while (clock64() - t0 < 100000) {
+          }
+        } else {
+          // drain the copies this thread issued before leaving
+          for (int s = 0; s < STAGES; ++s)
+            if (last_issue[s] >= 0)
+              wait_bar<PAIR>(&full_bar[s], (uint32_t)(last_issue[s] / STAGES) & 1u, abort_flag, p.status, false,
+                             p.wait_limit);
+        }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_mma(BM, BN, TF32);
+    if (lane == 0 && PAIR && rank == 1) {
+      // odd CTA of a pair: the even CTA's last commit means that every
+      // product reading this CTA's stages or writing its accumulators is done
+      wait_bar<true>(&drain_bar, 0, abort_flag, p.status, false, p.wait_limit);
+    } else if (lane == 0) {
+      constexpr uint32_t idesc = idesc_mma(PAIR ? 2 * BM : BM, BN, TF32);
       uint32_t it = 0, acc = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++acc) {
+      for (int u = cta0; u < n_units && ok; u += ncta, ++acc) {
         const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
-        if (!wait_bar(&acce_bar[buf], aph ^ 1u, abort_flag, p.status, true, p.wait_limit)) break;
+        if (!wait_bar<PAIR>(&acce_bar[buf], aph ^ 1u, abort_flag, p.status, true, p.wait_limit)) break;
         fence_after();
         const uint32_t d = tmem + buf * ACC_COLS;
         for (int kk = 0; kk < p.n_iter; ++kk, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
-          if (!wait_bar(XF ? &ready_bar[s] : &full_bar[s], ph, abort_flag, p.status, true, p.wait_limit)) {
+          if (!wait_bar<PAIR>(XF ? &ready_bar[s] : &full_bar[s], ph, abort_flag, p.status, true, p.wait_limit)) {
             ok = false;
             break;
           }
           fence_after();
           const uint32_t a = smem_u32(smem + (size_t)s * STAGE_BYTES);
           const uint32_t b = a + NP * A_BYTES;
+          auto step = [&](uint32_t dd, uint32_t aa, uint32_t bb, uint32_t accum) {
+            if (PAIR) {
+              if (TF32) mma_tf32_pair(dd, umma_desc(aa), umma_desc(bb), idesc, accum);
+              else mma_bf16_pair(dd, umma_desc(aa), umma_desc(bb), idesc, accum);
+            } else {
+              mma_step<TF32>(dd, umma_desc(aa), umma_desc(bb), idesc, accum);
+            }
+          };
           if (kk >= p.n_iter1) {
             // folded 1x1 operand (never the first K step of a unit); its M
             // tiles are whole 128-pixel blocks of the box
@@ -448,14 +627,15 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
               const uint32_t ai = a + i * BM * 128, di = d + i * BN;
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
-                mma_step<TF32>(di, umma_desc(ai + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
+                step(di, ai + 32 * k, b + 32 * k, 1u);
                 if (SPLIT) {
-                  mma_step<TF32>(di, umma_desc(ai + A_BYTES + 32 * k), umma_desc(b + 32 * k), idesc, 1u);
-                  mma_step<TF32>(di, umma_desc(ai + 32 * k), umma_desc(b + NB * B_BYTES + 32 * k), idesc, 1u);
+                  step(di, ai + A_BYTES + 32 * k, b + 32 * k, 1u);
+                  step(di, ai + 32 * k, b + NB * B_BYTES + 32 * k, 1u);
                 }
               }
             }
-            mma_commit(&empty_bar[s]);
+            if (PAIR) mma_commit_pair(&empty_bar[s]);
+            else mma_commit(&empty_bar[s]);
             continue;
           }
 #pragma unroll
@@ -468,23 +648,25 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
               const uint32_t at = a + i * A_ROW + (DXR ? 128 * t : 0), di = d + i * BN;
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
-                mma_step<TF32>(di, umma_desc(at + 32 * k), umma_desc(bt + 32 * k), idesc,
-                               (kk > 0 || t > 0 || k > 0) ? 1u : 0u);
+                step(di, at + 32 * k, bt + 32 * k, (kk > 0 || t > 0 || k > 0) ? 1u : 0u);
                 if (SPLIT) {
-                  mma_step<TF32>(di, umma_desc(at + A_BYTES + 32 * k), umma_desc(bt + 32 * k), idesc, 1u);
-                  mma_step<TF32>(di, umma_desc(at + 32 * k), umma_desc(bt + NB * B_BYTES + 32 * k), idesc, 1u);
+                  step(di, at + A_BYTES + 32 * k, bt + 32 * k, 1u);
+                  step(di, at + 32 * k, bt + NB * B_BYTES + 32 * k, 1u);
                 }
               }
             }
           }
-          mma_commit(&empty_bar[s]);
+          if (PAIR) mma_commit_pair(&empty_bar[s]);
+          else mma_commit(&empty_bar[s]);
         }
         if (!ok) break;
-        mma_commit(&accf_bar[buf]);
+        if (PAIR) mma_commit_pair(&accf_bar[buf]);
+        else mma_commit(&accf_bar[buf]);
       }
       // every MMA this thread issued has completed once this commit arrives
-      mma_commit(&drain_bar);
-      wait_bar(&drain_bar, 0, abort_flag, p.status, false, p.wait_limit);
+      if (PAIR) mma_commit_pair(&drain_bar);
+      else mma_commit(&drain_bar);
+      wait_bar<PAIR>(&drain_bar, 0, abort_flag, p.status, false, p.wait_limit);
     }
   } else if (!XF || warp < 6) {
     const int q = warp & 3;
@@ -503,20 +685,22 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
       return w * (HW / 4) + (int64_t)(yy >> 1) * (p.W >> 1) + (xx >> 1);
     };
     auto load_res = [&](int uu, int i, int c) {
-      const int64_t mm = res_index((int64_t)(uu / p.n_tiles) * (BM * MT) + i * BM + row);
+      const int64_t mm = res_index(unit_m0(uu) + i * BM + row);
       const float4* src = reinterpret_cast<const float4*>(p.res + mm * p.Cout + (uu % p.n_tiles) * BN + c);
 #pragma unroll
       for (int j = 0; j < 8; ++j) nx[j] = src[j];
     };
-    if (p.res && (int)blockIdx.x < n_units) load_res(blockIdx.x, 0, 0);
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++acc) {
+    if (p.res && cta0 < n_units) load_res(cta0, 0, 0);
+    // PAIR: the accumulator is released on the even CTA's barrier
+    const uint32_t acce_remote = PAIR && rank == 1 ? peer_addr(&acce_bar[0], 0) : 0u;
+    for (int u = cta0; u < n_units; u += ncta, ++acc) {
       const uint32_t buf = acc & 1u, aph = (acc >> 1) & 1u;
-      if (!wait_bar(&accf_bar[buf], aph, abort_flag, p.status, true, p.wait_limit)) break;
+      if (!wait_bar<PAIR>(&accf_bar[buf], aph, abort_flag, p.status, true, p.wait_limit)) break;
       fence_after();
       const int n0 = (u % p.n_tiles) * BN;
 #pragma unroll 1
       for (int i = 0; i < MT; ++i) {
-        const int64_t m = (int64_t)(u / p.n_tiles) * (BM * MT) + i * BM + row;
+        const int64_t m = unit_m0(u) + i * BM + row;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
           float4 rv[8];
@@ -525,7 +709,7 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
             for (int j = 0; j < 8; ++j) rv[j] = nx[j];
             if (c0 + 32 < BN) load_res(u, i, c0 + 32);
             else if (i + 1 < MT) load_res(u, i + 1, 0);
-            else if (u + (int)gridDim.x < n_units) load_res(u + gridDim.x, 0, 0);
+            else if (u + ncta < n_units) load_res(u + ncta, 0, 0);
           }
           uint32_t r[32];
           tmem_ld32(tmem + buf * ACC_COLS + i * BN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
@@ -579,7 +763,8 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
         }
       }
       fence_before();
-      mbar_arrive(&acce_bar[buf]);
+      if (PAIR && rank == 1) mbar_arrive_remote(acce_remote + 8u * buf);
+      else mbar_arrive(&acce_bar[buf]);
     }
   } else if constexpr (XF) {
     // Transform warpgroup (XF).  Thread t owns the 16-byte chunk t % 8 of
@@ -668,7 +853,17 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
   }
   fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (PAIR) {
+    // neither CTA leaves (or frees its tensor memory) while the other may
+    // still signal its barriers
+    cluster_sync();
+    if (warp == 1) {
+      __syncwarp();
+      fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS)
+                   : "memory");
+    }
+  } else if (warp == 1) {
     __syncwarp();
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS)
@@ -699,33 +894,82 @@ int sm_count() {
   return n;
 }
 
+int g_pair_clusters = 0;  // co-resident CTA pairs of the last pair kernel set up
+
 struct Maps {
   CUtensorMap a, b, alo, blo;      // main operand (and low parts)
   CUtensorMap a2, b2, a2lo, b2lo;  // folded 1x1 operand (copies of the above when absent)
 };
 
-// Shared memory of one stage, as the kernel lays it out.
-constexpr int stage_bytes(int BN, bool SPLIT, bool DXR, int MT) {
-  return (SPLIT ? 2 : 1) * ((((DXR ? (BM + 2) * 128 : BM * 128) * MT + 1023) / 1024 * 1024) + (DXR ? 3 : 1) * BN * 128);
+// Shared memory of one stage, as the kernel lays it out (PAIR: half the
+// weight rows).
+constexpr int stage_bytes(int BN, bool SPLIT, bool DXR, int MT, bool PAIR = false) {
+  return (SPLIT ? 2 : 1) * ((((DXR ? (BM + 2) * 128 : BM * 128) * MT + 1023) / 1024 * 1024) +
+                            (DXR ? 3 : 1) * (PAIR ? BN / 2 : BN) * 128);
 }
 
-template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF = false>
+template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF = false, bool PAIR = false>
 bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err) {
-  constexpr size_t smem = (size_t)STAGES * stage_bytes(BN, SPLIT, DXR, MT) + 1024;
+  constexpr size_t smem = (size_t)STAGES * stage_bytes(BN, SPLIT, DXR, MT, PAIR) + 1024;
   static_assert(smem <= 227 * 1024, "stages exceed the shared memory of a CTA");
   static_assert(2 * MT * BN <= 512, "accumulators exceed tensor memory");
   static bool attr = false;
-  auto kern = conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32, MT, XF>;
+  static int max_pairs = 0;
+  auto kern = conv_tc_kernel<BN, STAGES, SPLIT, DXR, TF32, MT, XF, PAIR>;
   if (!attr) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       *err = "cudaFuncSetAttribute failed";
       return false;
     }
+    if (PAIR) {
+      // co-resident clusters of two (one pair per TPC at most)
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * (unsigned)(sm_count() / 2));
+      cfg.blockDim = dim3(192);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        *err = "no co-resident CTA pairs for the tensor-core convolution";
+        return false;
+      }
+      max_pairs = n;
+      g_pair_clusters = n;
+    }
     attr = true;
   }
-  const int units = p.m_tiles / MT * p.n_tiles;
-  const int grid = units < sm_count() ? units : sm_count();
-  kern<<<grid, XF ? 192 + XF_THREADS : 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo, m.b2lo, p);
+  const int units = p.m_tiles / (PAIR ? 2 * MT : MT) * p.n_tiles;
+  if (PAIR) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    const int pairs = units < max_pairs ? units : max_pairs;
+    cfg.gridDim = dim3(2 * (unsigned)pairs);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo, m.b2lo, p);
+    if (le != cudaSuccess) {
+      cudaGetLastError();
+      *err = cudaGetErrorString(le);
+      return false;
+    }
+  } else {
+    const int grid = units < sm_count() ? units : sm_count();
+    kern<<<grid, XF ? 192 + XF_THREADS : 192, smem, st>>>(m.a, m.b, m.alo, m.blo, m.a2, m.b2, m.a2lo, m.b2lo, p);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -735,6 +979,8 @@ bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err)
 }
 
 }  // namespace
+
+int conv_tc_pair_clusters() { return g_pair_clusters; }
 
 bool conv_tc_supported(int cin, int cout, int ks) {
   return (ks == 1 || ks == 2 || ks == 3) && cin >= 64 && cin % 64 == 0 && cout >= 64 && cout % 64 == 0 &&
@@ -824,11 +1070,18 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  // weights [tap][Cout][C]; box of kch channels x BN rows
+  // CTA pairs (cta_group::2): plain operands, and every CTA's MT M tiles
+  // paired with the next MT (an even number of unit halves).  pair == 1
+  // requires them, pair == 2 takes them where the shape allows.
+  const int64_t m_tiles = (int64_t)n * H * W / BM;
+  const bool pair_shape = !split && !xf;
+  bool pair = tile && (tile->pair == 1 || (tile->pair == 2 && pair_shape));
+  // weights [tap][Cout][C]; box of kch channels x BN rows (a pair's CTA
+  // stages BN / 2 of them)
   auto encB = [&](CUtensorMap* mp, const void* ptr, int C, int taps) {
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)taps * Cout};
     cuuint64_t strides[1] = {(cuuint64_t)C * es};
-    cuuint32_t box[2] = {(cuuint32_t)kch, (cuuint32_t)BN};
+    cuuint32_t box[2] = {(cuuint32_t)kch, (cuuint32_t)(pair ? BN / 2 : BN)};
     cuuint32_t ones[2] = {1, 1};
     return enc(mp, dt, 2, (void*)ptr, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -844,6 +1097,13 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
       return false;
     }
     mt = tile->mt;
+  }
+  // preferred pairs: where measured faster (N tiles of 128 or 256 weight
+  // rows; the 64-channel row-reuse layers stay on one CTA)
+  if (pair && tile->pair == 2 && (m_tiles % (2 * mt) != 0 || BN < 128 || dxr)) pair = false;
+  if (pair && (!pair_shape || m_tiles % (2 * mt) != 0)) {
+    *err = "invalid tile shape (CTA pair): needs plain operands and an even number of unit halves";
+    return false;
   }
   const int abw = dxr ? W + 2 : W, abh = dxr ? mt : mt * 128 / W;
   if (!encA(&m.a, x, Cin, abw, abh) || !encB(&m.b, w, Cin, ks * ks)) {
@@ -925,6 +1185,32 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
         case 256: return launch<256, 4, false, false, true, 1, true>(m, p, st, err);
       }
     }
+    *err = "unsupported N tile";
+    return false;
+  }
+  if (pair) {
+    // stages: about 180-205 KB per CTA (a third fewer bytes per stage)
+#define IDF_TC_PAIR(TF)                                                                       \
+    if (mt == 2) {                                                                            \
+      switch (BN) {                                                                           \
+        case 64: return dxr ? launch<64, 4, false, true, TF, 2, false, true>(m, p, st, err)   \
+                            : launch<64, 5, false, false, TF, 2, false, true>(m, p, st, err); \
+        case 128: return launch<128, 5, false, false, TF, 2, false, true>(m, p, st, err);     \
+      }                                                                                       \
+    } else {                                                                                  \
+      switch (BN) {                                                                           \
+        case 64: return dxr ? launch<64, 6, false, true, TF, 1, false, true>(m, p, st, err)   \
+                            : launch<64, 8, false, false, TF, 1, false, true>(m, p, st, err); \
+        case 128: return launch<128, 8, false, false, TF, 1, false, true>(m, p, st, err);     \
+        case 256: return launch<256, 6, false, false, TF, 1, false, true>(m, p, st, err);     \
+      }                                                                                       \
+    }
+    if (tf32) {
+      IDF_TC_PAIR(true)
+    } else {
+      IDF_TC_PAIR(false)
+    }
+#undef IDF_TC_PAIR
     *err = "unsupported N tile";
     return false;
   }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <map>
 #include <vector>
 
 namespace idf {
@@ -179,6 +180,13 @@ struct Prof {
         flops[r.kind] += r.flops;
         bytes[r.kind] += r.bytes;
         launches[r.kind]++;
+        if (r.kind == 0) {
+          // tensor-core convolutions by launch shape (FLOPs, algorithmic
+          // bytes): a per-launch roofline needs both
+          auto& e = conv_shapes[{r.flops, r.bytes}];
+          e.first++;
+          e.second += t;
+        }
       }
       pool.push_back(r.a);
       pool.push_back(r.b);
@@ -188,7 +196,9 @@ struct Prof {
   }
   void reset() {
     for (int k = 0; k < PK_COUNT; ++k) ms[k] = flops[k] = bytes[k] = 0, launches[k] = 0;
+    conv_shapes.clear();
   }
+  std::map<std::pair<double, double>, std::pair<int64_t, double>> conv_shapes;  // -> (launches, ms)
   ~Prof() {
     for (auto e : pool) cudaEventDestroy(e);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -222,9 +232,17 @@ int64_t unet_launches(const UNet* u);
 // device status word set by bounded device-side waits that ran out
 int* unet_status(const UNet* u);
 // fuse_groupnorm (IDF_TF32 only): GroupNorm and SiLU inside the tensor-core
-// convolutions' operand path; wait_limit: clock64 cycles a bounded device
-// wait may take (0: about 0.5 s)
-void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit, bool autotune = false);
+// convolutions' operand path;
+// wait_limit: clock64 cycles a bounded device wait may take (0: about
+// 0.5 s); graphs: replay repeated forwards (same x_in, n, F, bias) as one
+// CUDA graph launch (bitwise the same kernels and arguments)
+// pairs: tensor-core convolutions on clusters of two CTAs (cta_group::2)
+// wherever the operands and shape allow them
+void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit, bool autotune = false,
+                      bool graphs = false, bool pairs = false);
+// CUDA-graph summary: forwards captured, forwards replayed, kernels those
+// replays ran
+void unet_graph_stats(const UNet* u, int64_t* captures, int64_t* replays, int64_t* kernels);
 // autotuner summary: layer classes tuned, and those whose fastest tile shape
 // differs from the built-in choice
 void unet_autotune_stats(const UNet* u, int* tuned, int* changed);
@@ -232,6 +250,8 @@ void unet_set_prof(UNet* u, Prof* p);
 
 // tcgen05 conv (conv_tc.cu)
 bool conv_tc_supported(int cin, int cout, int ks);
+// co-resident clusters of two CTAs the pair kernels launch with (0 before the first)
+int conv_tc_pair_clusters();
 bool conv_tc_shape_ok(int H, int W);
 
 // Geometry options of a tensor-core convolution: the input offset of tap
@@ -264,6 +284,7 @@ struct TcXf {
 // same result bit for bit (the K order of each output element is fixed).
 struct TcTile {
   int bn = 0, mt = 0, dxr = -1;
+  int pair = -1;  // 1: clusters of two CTAs issuing cta_group::2 products; 0 / -1: one CTA
 };
 // The valid tile shapes of a convolution (for autotuning).
 std::vector<TcTile> conv_tc_tiles(int H, int W, int Cin, int Cout, int ks, bool split, bool xf,

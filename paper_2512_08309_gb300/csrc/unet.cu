@@ -1591,8 +1591,28 @@ struct UNet {
   // tile-shape autotuner: per (convolution, geometry, batch class) the
   // fastest valid shape, measured once on the first launch of that class
   bool autotune = false;
+  bool pairs = false;  // tensor-core convolutions on CTA pairs (cta_group::2) where the shape allows
   std::map<std::tuple<const void*, int, int, int, int>, TcTile> tuned;
   int tuned_changed = 0;
+  // CUDA graphs: a forward's launch sequence depends only on (x_in, n, F,
+  // bias) (all other buffers are the network's own), so the second forward
+  // with the same four arguments is captured once and every later one is a
+  // single graph launch.  A one-off shape (the last, partial batch of a
+  // round) runs eagerly and is never captured.
+  bool graphs = false;
+  struct Graph {
+    const float* x;
+    int n;
+    float* F;
+    const float* bias;
+    int seen = 0;                    // eager forwards with this key so far
+    cudaGraphExec_t exec = nullptr;  // set once captured
+    int64_t kernels = 0;             // kernel nodes of the captured forward
+    uint64_t used = 0;               // LRU stamp
+  };
+  std::vector<Graph> gcache;
+  uint64_t gclock = 0;
+  int64_t graph_captures = 0, graph_replays = 0, graph_kernels = 0;
 };
 
 static bool uses_small(const UNetDesc& d, int precision) {
@@ -1686,6 +1706,8 @@ void unet_destroy(UNet* u) {
   cudaFree(u->blkmem);
   cudaFree(u->status);
   small_net_destroy(u->small);
+  for (auto& g : u->gcache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   delete u;
 }
 
@@ -1920,10 +1942,24 @@ UNet* unet_create(const UNetDesc& d, const float* w_host, int precision, int max
 int unet_max_batch(const UNet* u) { return u->max_batch; }
 int64_t unet_launches(const UNet* u) { return u->launches; }
 int* unet_status(const UNet* u) { return u->status; }
-void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit, bool autotune) {
+static void drop_graphs(UNet* u) {
+  for (auto& g : u->gcache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  u->gcache.clear();
+}
+void unet_set_options(UNet* u, bool fuse_groupnorm, long long wait_limit, bool autotune, bool graphs,
+                      bool pairs) {
   u->fuse_gn = fuse_groupnorm && u->precision == 4;
   u->wait_limit = wait_limit;
   u->autotune = autotune;
+  u->pairs = pairs;
+  u->graphs = graphs && !u->small;
+  drop_graphs(u);  // captured launches carry the old options
+}
+void unet_graph_stats(const UNet* u, int64_t* captures, int64_t* replays, int64_t* kernels) {
+  *captures = u ? u->graph_captures : 0;
+  *replays = u ? u->graph_replays : 0;
+  *kernels = u ? u->graph_kernels : 0;
 }
 void unet_autotune_stats(const UNet* u, int* tuned, int* changed) {
   *tuned = u ? (int)u->tuned.size() : 0;
@@ -2024,6 +2060,13 @@ bool conv_run(Ctx& c, const ConvW& w, const void* x, bool x_f32, const float* re
         it = c.u->tuned.emplace(key, best).first;
       }
       if (it->second.bn) chosen = &it->second;
+    }
+    // CTA pairs where the shape allows them (same products per element)
+    TcTile pt{};
+    if (c.u->pairs) {
+      if (chosen) pt = *chosen;
+      pt.pair = 2;
+      chosen = &pt;
     }
     const int pr = c.u->prof ? c.u->prof->begin(PK_CONV_TC, c.st, flops, by) : -1;
     const bool ok = launch(chosen);
@@ -2707,9 +2750,75 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
     }
     return ok;
   }
-  if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err, bias);
-  if (u->precision == 4) return forward_t<tf32>(u, x_in, n, F, st, err, bias);
-  return forward_t<float>(u, x_in, n, F, st, err, bias);
+  auto eager = [&]() {
+    if (u->precision == 1 || u->precision == 3) return forward_t<bf16>(u, x_in, n, F, st, err, bias);
+    if (u->precision == 4) return forward_t<tf32>(u, x_in, n, F, st, err, bias);
+    return forward_t<float>(u, x_in, n, F, st, err, bias);
+  };
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!u->graphs || (u->prof && u->prof->on) || !st || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone)
+    return eager();
+  UNet::Graph* g = nullptr;
+  for (auto& e : u->gcache)
+    if (e.x == x_in && e.n == n && e.F == F && e.bias == bias) g = &e;
+  if (!g) {
+    // first forward with this key: eager (this also tunes its tile shapes)
+    constexpr size_t MAX_GRAPHS = 24;
+    if (u->gcache.size() >= MAX_GRAPHS) {
+      size_t v = 0;
+      for (size_t i = 1; i < u->gcache.size(); ++i)
+        if (u->gcache[i].used < u->gcache[v].used) v = i;
+      if (u->gcache[v].exec) cudaGraphExecDestroy(u->gcache[v].exec);
+      u->gcache.erase(u->gcache.begin() + (std::ptrdiff_t)v);
+    }
+    UNet::Graph ng;
+    ng.x = x_in; ng.n = n; ng.F = F; ng.bias = bias; ng.seen = 1; ng.used = ++u->gclock;
+    u->gcache.push_back(ng);
+    return eager();
+  }
+  g->used = ++u->gclock;
+  if (!g->exec) {
+    if (g->seen < 0) return eager();  // capture failed once: stay eager
+    const int64_t l0 = u->launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      g->seen = -1;
+      return eager();
+    }
+    const bool ok = eager();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    const int64_t kernels = u->launches - l0;
+    u->launches = l0;  // nothing ran yet
+    if (!ok) {
+      // a host-side failure inside the forward (its message is in err)
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return false;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (ec != cudaSuccess || !graph || cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      g->seen = -1;
+      return eager();
+    }
+    cudaGraphDestroy(graph);
+    g->exec = ex;
+    g->kernels = kernels;
+    ++u->graph_captures;
+  }
+  const cudaError_t e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) {
+    err->code = 3;
+    err->msg = std::string("UNet graph launch: ") + cudaGetErrorString(e);
+    return false;
+  }
+  u->launches += g->kernels;
+  ++u->graph_replays;
+  u->graph_kernels += g->kernels;
+  return true;
 }
 
 // ------------------------------------------------------------ float32 building blocks

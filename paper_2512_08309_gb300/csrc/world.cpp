@@ -1340,7 +1340,8 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
       }
       unet_set_prof(L.unet, &W->prof);
       unet_set_options(L.unet, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles,
-                       opts->autotune != 0);
+                       opts->autotune != 0, opts->cuda_graphs != 0,
+                       opts->cta_pairs != 0);
       const idf_level_desc& dsrc = stack->level[i];
       if (dsrc.cond_dim > 0) {
         // the embedding E is the last (channels[0], cond_dim, 1, 1) tensor
@@ -1363,7 +1364,8 @@ idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack, const i
         if (!L.guide) return bail(e.code == 2 ? IDF_ENOMEM : IDF_ECUDA);
         unet_set_prof(L.guide, &W->prof);
         unet_set_options(L.guide, opts->groupnorm_in_conv != 0, (long long)opts->device_wait_budget_cycles,
-                         opts->autotune != 0);
+                         opts->autotune != 0, opts->cuda_graphs != 0,
+                       opts->cta_pairs != 0);
         L.w_guide = (float)dsrc.guidance;
       }
     }
@@ -1502,11 +1504,41 @@ idf_status idf_world_stats(const idf_world* Wc, char* buf, size_t len) {
     tuned += t;
     changed += c;
   }
-  char b[256];
+  int64_t gcap = 0, grep = 0, gker = 0;
+  for (const Level& L : W->lv)
+    for (const UNet* u : {L.unet, L.guide}) {
+      int64_t a = 0, r = 0, k = 0;
+      unet_graph_stats(u, &a, &r, &k);
+      gcap += a;
+      grep += r;
+      gker += k;
+    }
+  char b[512];
+  // host launch calls: every kernel launched eagerly, plus one per graph replay
   snprintf(b, sizeof b,
-           "], \"kernel_launches\": %lld, \"queries\": %lld, \"autotune\": {\"tuned\": %d, \"changed\": %d}",
-           (long long)W->launches, (long long)W->queries, tuned, changed);
+           "], \"kernel_launches\": %lld, \"queries\": %lld, \"autotune\": {\"tuned\": %d, \"changed\": %d}, "
+           "\"graphs\": {\"captured\": %lld, \"replays\": %lld, \"replayed_kernels\": %lld, "
+           "\"host_launch_calls\": %lld}",
+           (long long)W->launches, (long long)W->queries, tuned, changed, (long long)gcap, (long long)grep,
+           (long long)gker, (long long)(W->launches - gker + grep));
   s += b;
+  // the device status words as they stand (read, not cleared): a bounded
+  // wait of a level's tensor-core kernels that ran out, a bounds check that
+  // fired.  Calls that synchronize (queries) fail on them; an asynchronous
+  // idf_unet_forward leaves them here.
+  {
+    int waits = 0, checks = 0;
+    for (const Level& L : W->lv)
+      for (const UNet* u : {L.unet, L.guide}) {
+        int t = 0;
+        if (u && cudaMemcpy(&t, unet_status(u), sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && t) ++waits;
+      }
+    if (W->d_err) cudaMemcpy(&checks, W->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    char d[128];
+    snprintf(d, sizeof d, ", \"device_status\": {\"waits_expired\": %d, \"bounds_check\": %d}, "
+             "\"cta_pair_clusters\": %d", waits, checks ? 1 : 0, conv_tc_pair_clusters());
+    s += d;
+  }
   static const char* names[PK_COUNT] = {"conv_tc", "conv_simt", "groupnorm", "attention", "resample",
                                         "gather", "test_denoiser", "blend", "assemble", "decode"};
   s += ", \"profile\": {";
@@ -1517,7 +1549,18 @@ idf_status idf_world_stats(const idf_world* Wc, char* buf, size_t len) {
              W->prof.bytes[k]);
     s += e;
   }
-  s += "}}";
+  s += "}, \"conv_tc_shapes\": [";
+  {
+    bool first = true;
+    for (const auto& kv : W->prof.conv_shapes) {
+      char e[160];
+      snprintf(e, sizeof e, "%s[%.6e, %.6e, %lld, %.6f]", first ? "" : ", ", kv.first.first, kv.first.second,
+               (long long)kv.second.first, kv.second.second);
+      s += e;
+      first = false;
+    }
+  }
+  s += "]}";
   if (s.size() + 1 > len) return IDF_EINVAL;
   memcpy(buf, s.c_str(), s.size() + 1);
   return IDF_OK;
