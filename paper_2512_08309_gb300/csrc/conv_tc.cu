@@ -978,6 +978,217 @@ bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err)
   return true;
 }
 
+
+// ------------------------------------------------------------ attention
+// Self-attention of one window and one head on the tensor cores (the
+// attention block at the bottom of the fine UNet, Sec. 5.3): 256 tokens
+// (16 x 16 pixels), head width 64.  Q, K and V (float32, from the qkv
+// projection) are staged in shared memory in the 128-byte swizzled K-major
+// layout: Q and K with the tokens as rows, each as a bfloat16 high part and
+// the bfloat16 rounding of its remainder (x = hi + lo), V rounded to bfloat16
+// and transposed (head channels as rows, tokens along K).  For each of the
+// two 128-query M tiles: S = Q K^T (M = 128, N = 256, K = 64) into tensor
+// memory as Qhi Khi + Qlo Khi + Qhi Klo (the scores go through exp, so their
+// rounding is compensated; bfloat16 alone moved the fine network's output by
+// several 1e-3 sigma);
+// every thread owns one query row, takes its maximum, p = exp((s - max) / 8)
+// and the row sum in float32, and writes p as bfloat16 in the same swizzled
+// layout (four 64-key K chunks); then O = P V (M = 128, N = 64, K = 256) into
+// tensor memory, and O / sum leaves as the operand of the output projection.
+// The products are bfloat16 with float32 accumulation; the softmax is
+// float32.  Every wait is bounded (status word, as the convolutions).
+template <bool OUT_TF32>
+__global__ void __launch_bounds__(128, 1) attention_tc_kernel(const float* __restrict__ qkv, int C, int heads,
+                                                              void* __restrict__ out, int* status,
+                                                              long long wait_limit) {
+  constexpr int TN = 256, D = 64;
+  constexpr int Q_OFF = 0, QL_OFF = 32768, K_OFF = 65536, KL_OFF = 98304, V_OFF = 131072, P_OFF = 163840;
+  extern __shared__ uint8_t dsmem[];
+  uint8_t* sm = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int skip_sh;
+  __shared__ int abort_sh;
+  const int b = blockIdx.x / heads, h = blockIdx.x % heads;
+  const int tid = threadIdx.x, warp = tid / 32;
+  if (tid == 0) {
+    skip_sh = *(volatile int*)status;
+    abort_sh = 0;
+  }
+  __syncthreads();
+  if (skip_sh) return;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // 8 bfloat16 values as one 16-byte chunk
+  auto pack8 = [](const float* v) {
+    uint4 r;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 t = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&t);
+    }
+    return r;
+  };
+  // the same for the bfloat16 remainders x - bf16(x)
+  auto pack8_lo = [&](const float* v) {
+    float l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l[i] = v[i] - __bfloat162float(__float2bfloat16_rn(v[i]));
+    return pack8(l);
+  };
+  const float* base = qkv + (int64_t)b * TN * 3 * C + h * D;
+  // Q and K: chunk j (channels 8j .. 8j + 7) of token t at row t, physical
+  // chunk j ^ (t % 8)
+  // (unrolled so that several global loads of each thread are in flight)
+#pragma unroll 4
+  for (int e = tid; e < TN * 8; e += 128) {
+    const int t = e >> 3, j = e & 7;
+    float v[8];
+    const float4* q = reinterpret_cast<const float4*>(base + (int64_t)t * 3 * C + 8 * j);
+    const int o = t * 128 + ((j ^ (t & 7)) << 4);
+    *reinterpret_cast<float4*>(v) = q[0];
+    *reinterpret_cast<float4*>(v + 4) = q[1];
+    *reinterpret_cast<uint4*>(sm + Q_OFF + o) = pack8(v);
+    *reinterpret_cast<uint4*>(sm + QL_OFF + o) = pack8_lo(v);
+    const float4* k = reinterpret_cast<const float4*>(base + (int64_t)t * 3 * C + C + 8 * j);
+    *reinterpret_cast<float4*>(v) = k[0];
+    *reinterpret_cast<float4*>(v + 4) = k[1];
+    *reinterpret_cast<uint4*>(sm + K_OFF + o) = pack8(v);
+    *reinterpret_cast<uint4*>(sm + KL_OFF + o) = pack8_lo(v);
+  }
+  // V^T: row d of K chunk c holds tokens 64c .. 64c + 63; tokens 8g .. 8g + 7
+  // of a chunk form logical chunk g
+#pragma unroll 4
+  for (int e = tid; e < D * (TN / 8); e += 128) {
+    const int d = e % D, tg = e / D, t0 = 8 * tg;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = base[(int64_t)(t0 + i) * 3 * C + 2 * C + d];
+    const int c = t0 / 64, g = (t0 % 64) / 8;
+    *reinterpret_cast<uint4*>(sm + V_OFF + c * 8192 + d * 128 + ((g ^ (d & 7)) << 4)) = pack8(v);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_sh;
+  const uint32_t S_COL = 0, O_COL = 256;
+  const int r = tid;  // query row of the M tile = TMEM lane
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  volatile int* abort_flag = &abort_sh;
+  uint32_t uses = 0;  // completed phases of bar
+  bool ok = true;
+  for (int m = 0; m < 2 && ok; ++m) {
+    if (tid == 0) {
+      constexpr uint32_t idS = idesc_mma(128, 256, false);
+      const uint32_t a = smem_u32(sm + Q_OFF + m * 16384), al = smem_u32(sm + QL_OFF + m * 16384);
+      const uint32_t bk = smem_u32(sm + K_OFF), bl = smem_u32(sm + KL_OFF);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        mma_bf16(tmem + S_COL, umma_desc(a + 32 * k), umma_desc(bk + 32 * k), idS, k > 0);
+        mma_bf16(tmem + S_COL, umma_desc(al + 32 * k), umma_desc(bk + 32 * k), idS, 1u);
+        mma_bf16(tmem + S_COL, umma_desc(a + 32 * k), umma_desc(bl + 32 * k), idS, 1u);
+      }
+      mma_commit(&bar);
+    }
+    // every thread takes the same decision (a lone timeout must not split
+    // the block at the barriers below)
+    if (!__syncthreads_and(wait_bar(&bar, uses & 1u, abort_flag, status, true, wait_limit))) {
+      ok = false;
+      break;
+    }
+    ++uses;
+    fence_after();
+    float mx = -INFINITY;
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_off + S_COL + c0, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) mx = fmaxf(mx, __uint_as_float(v[i]));
+    }
+    float sum = 0.0f;
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_off + S_COL + c0, v);
+      float pv[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        pv[i] = __expf((__uint_as_float(v[i]) - mx) * 0.125f);
+        sum += pv[i];
+      }
+      const int c = c0 / 64;
+#pragma unroll
+      for (int g4 = 0; g4 < 4; ++g4) {
+        const int g = (c0 % 64) / 8 + g4;
+        *reinterpret_cast<uint4*>(sm + P_OFF + c * 16384 + r * 128 + ((g ^ (r & 7)) << 4)) = pack8(pv + 8 * g4);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+      constexpr uint32_t idO = idesc_mma(128, 64, false);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t a = smem_u32(sm + P_OFF + c * 16384), bv = smem_u32(sm + V_OFF + c * 8192);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16(tmem + O_COL, umma_desc(a + 32 * k), umma_desc(bv + 32 * k), idO, (c | k) > 0);
+      }
+      mma_commit(&bar);
+    }
+    if (!__syncthreads_and(wait_bar(&bar, uses & 1u, abort_flag, status, true, wait_limit))) {
+      ok = false;
+      break;
+    }
+    ++uses;
+    fence_after();
+    const float inv = 1.0f / sum;
+    const int64_t row = (int64_t)b * TN + m * 128 + r;
+#pragma unroll
+    for (int c0 = 0; c0 < D; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_off + O_COL + c0, v);
+      float o[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) o[i] = __uint_as_float(v[i]) * inv;
+      if (OUT_TF32) {
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + row * C + h * D + c0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          dst[i] = make_float4(xf_tf32(o[4 * i]), xf_tf32(o[4 * i + 1]), xf_tf32(o[4 * i + 2]), xf_tf32(o[4 * i + 3]));
+      } else {
+        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + row * C + h * D + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = pack8(o + 8 * i);
+      }
+    }
+    fence_before();
+    __syncthreads();  // S and O are free for the next M tile
+    fence_after();
+  }
+  if (!ok) {
+    // let the products already issued finish before freeing their memory
+    wait_bar(&bar, uses & 1u, abort_flag, status, false, wait_limit);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 }  // namespace
 
 int conv_tc_pair_clusters() { return g_pair_clusters; }
@@ -1249,6 +1460,34 @@ bool conv_tc_forward(const void* x, const void* w, const void* x_lo, const void*
   }
   *err = "unsupported N tile";
   return false;
+}
+
+
+bool attention_tc_supported(int Tn, int dh) { return Tn == 256 && dh == 64; }
+
+bool attention_tc_forward(const float* qkv, int n, int C, int heads, void* out, bool out_tf32, int* status,
+                          long long wait_limit, cudaStream_t st, std::string* err) {
+  if (C != heads * 64) {
+    *err = "attention: head width must be 64";
+    return false;
+  }
+  constexpr size_t smem = 229376 + 1024;
+  static bool attr[2] = {false, false};
+  auto kern = out_tf32 ? attention_tc_kernel<true> : attention_tc_kernel<false>;
+  if (!attr[out_tf32]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      *err = "cudaFuncSetAttribute failed";
+      return false;
+    }
+    attr[out_tf32] = true;
+  }
+  kern<<<n * heads, 128, smem, st>>>(qkv, C, heads, out, status, wait_limit > 0 ? wait_limit : 1000000000LL);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return false;
+  }
+  return true;
 }
 
 }  // namespace idf

@@ -252,6 +252,13 @@ void unet_set_prof(UNet* u, Prof* p);
 bool conv_tc_supported(int cin, int cout, int ks);
 // co-resident clusters of two CTAs the pair kernels launch with (0 before the first)
 int conv_tc_pair_clusters();
+// Self-attention on the tensor cores (bfloat16 products, float32 softmax and
+// accumulation): qkv float32 [n][Tn][3C] (Q, K, V; head h at channels
+// 64h .. 64h + 63 of each), out [n][Tn][C] as bfloat16, or as tf32-rounded
+// float32 (out_tf32).  Tn = 256 and head width 64 only.
+bool attention_tc_supported(int Tn, int dh);
+bool attention_tc_forward(const float* qkv, int n, int C, int heads, void* out, bool out_tf32, int* status,
+                          long long wait_limit, cudaStream_t st, std::string* err);
 bool conv_tc_shape_ok(int H, int W);
 
 // Geometry options of a tensor-core convolution: the input offset of tap

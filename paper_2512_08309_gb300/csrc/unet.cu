@@ -2654,7 +2654,17 @@ bool forward_t(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, Err
     const size_t smem = (size_t)2 * Tn * dh * sizeof(float);
     const int pr = u->prof ? u->prof->begin(PK_ATTENTION, st, 4.0 * n * (double)Tn * Tn * prev, 0.0) : -1;
     const size_t smem2 = (size_t)2 * Tn * (dh + 8) * sizeof(float);
-    if (dh == 64 && Tn % 4 == 0 && 2 * Tn <= 512 && smem2 <= 200 * 1024) {
+    constexpr bool tc_ta = std::is_same<TA, bf16>::value || std::is_same<TA, tf32>::value;
+    if (tc_ta && !u->split && attention_tc_supported(Tn, dh)) {
+      // tensor cores: bfloat16 products, float32 softmax and accumulation
+      std::string e;
+      if (!attention_tc_forward((const float*)bl.T2, n, prev, d.heads, bl.T3, std::is_same<TA, tf32>::value,
+                                u->status, u->wait_limit, st, &e)) {
+        c.ok = false;
+        c.err->code = 3;
+        c.err->msg = "attention: " + e;
+      }
+    } else if (dh == 64 && Tn % 4 == 0 && 2 * Tn <= 512 && smem2 <= 200 * 1024) {
       auto kern = attention_d2_kernel<TA, 64>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
       kern<<<n * d.heads, 2 * Tn, smem2, st>>>((const float*)bl.T2, Tn, prev, d.heads, (TA*)bl.T3,
@@ -2764,7 +2774,9 @@ bool unet_forward(UNet* u, const float* x_in, int n, float* F, cudaStream_t st, 
     if (e.x == x_in && e.n == n && e.F == F && e.bias == bias) g = &e;
   if (!g) {
     // first forward with this key: eager (this also tunes its tile shapes)
-    constexpr size_t MAX_GRAPHS = 24;
+    // a cold query of the 2-level stack meets about 50 keys (every full
+    // batch slot, and one partial batch per round and level)
+    constexpr size_t MAX_GRAPHS = 192;
     if (u->gcache.size() >= MAX_GRAPHS) {
       size_t v = 0;
       for (size_t i = 1; i < u->gcache.size(); ++i)
