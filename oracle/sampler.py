@@ -229,10 +229,19 @@ def cone_rects(lvl: _LevelCommon, y0, x0, h, w):
 
 
 class EagerLevel(_LevelCommon):
-    """Eq. 1 on a bounded canvas holding the cone of one region, all steps dense."""
+    """Eq. 1 on a bounded canvas holding the cone of one region.
 
-    def run(self, y0, x0, h, w):
+    Round k evaluates every window that covers a pixel of rects[k + 1] (the
+    region of J_{k+1} the result depends on) and forms J_{k+1} there: each
+    such pixel gets the sum over all windows that contain it, in the order
+    (i, j) ascending, so it equals the dense form (``dense=True``: every
+    window of rects[0] in every round) term for term; the dense form also
+    computes pixels nothing reads."""
+
+    def run(self, y0, x0, h, w, dense=False):
         rects = cone_rects(self, y0, x0, h, w)
+        if not dense:
+            return self._run_cone(rects, y0, x0, h, w)
         cy, cx, ch, cw = rects[0]
         J = self.sig[0] * self.noise(0, cy, cx, ch, cw)
         ni = (ch - self.H) // self.s + 1
@@ -252,6 +261,32 @@ class EagerLevel(_LevelCommon):
             J = np.zeros((ch, cw))
             nz = B != 0
             J[nz] = A[nz] / B[nz]
+        self._canvas = (cy, cx, J)
+        return J[y0 - cy:y0 - cy + h, x0 - cx:x0 - cx + w]
+
+    def _run_cone(self, rects, y0, x0, h, w):
+        H = self.H
+        cy, cx, ch, cw = rects[0]
+        J = self.sig[0] * self.noise(0, cy, cx, ch, cw)
+        for k in range(self.R):
+            ny, nx, nh, nw = rects[k + 1]
+            wins = K_.kappa(ny, nx, nh, nw, H, self.s, self.o)
+            rr = [K_.window_rect(i, j, H, self.s, self.o) for (i, j) in wins]
+            xs = [J[r[0] - cy:r[0] - cy + H, r[1] - cx:r[1] - cx + H] for r in rr]
+            phis = self.phi(k, xs, rr)
+            A = np.zeros((nh, nw))
+            B = np.zeros((nh, nw))
+            for r, p in zip(rr, phis):
+                # the part of window r inside rects[k + 1]
+                ya, yb = max(r[0], ny), min(r[0] + H, ny + nh)
+                xa, xb = max(r[1], nx), min(r[1] + H, nx + nw)
+                wp = (self.W * p)[ya - r[0]:yb - r[0], xa - r[1]:xb - r[1]]
+                A[ya - ny:yb - ny, xa - nx:xb - nx] += wp
+                B[ya - ny:yb - ny, xa - nx:xb - nx] += self.W[ya - r[0]:yb - r[0], xa - r[1]:xb - r[1]]
+            J = np.zeros((nh, nw))
+            nz = B != 0
+            J[nz] = A[nz] / B[nz]
+            cy, cx, ch, cw = ny, nx, nh, nw
         self._canvas = (cy, cx, J)
         return J[y0 - cy:y0 - cy + h, x0 - cx:x0 - cx + w]
 
@@ -296,15 +331,16 @@ class World:
                                 low_scale=st["low_scale"], res_scale=st["res_scale"])
 
 
-def eager_world_model(seed: int, stack: dict, weights: list, y0, x0, h, w):
+def eager_world_model(seed: int, stack: dict, weights: list, y0, x0, h, w, dense=False):
     """Eq. 1 brute force for the last level's result over a region; for a
     two-level stack the coarse level runs eagerly over the canvas the fine
-    cone's conditioning needs."""
+    cone's conditioning needs.  dense: every window of the canvas in every
+    round (EagerLevel)."""
     lvls = stack["level"]
     eps = stack.get("blend_eps", 1e-3)
     if len(lvls) == 1:
         e = EagerLevel(seed, lvls[0], 0, weights=weights[0] if weights else None, blend_eps=eps)
-        return e.run(y0, x0, h, w)
+        return e.run(y0, x0, h, w, dense=dense)
     fine_lv = lvls[1]
     fine = EagerLevel(seed, fine_lv, 1, weights=weights[1] if weights else None, blend_eps=eps)
     rects = cone_rects(fine, y0, x0, h, w)
@@ -313,9 +349,9 @@ def eager_world_model(seed: int, stack: dict, weights: list, y0, x0, h, w):
     coarse = EagerLevel(seed, lvls[0], 0, weights=weights[0] if weights else None, blend_eps=eps)
     qy0, qx0 = cy // f, cx // f
     qy1, qx1 = (cy + ch - 1) // f, (cx + cw - 1) // f
-    coarse.run(qy0, qx0, qy1 - qy0 + 1, qx1 - qx0 + 1)
+    coarse.run(qy0, qx0, qy1 - qy0 + 1, qx1 - qx0 + 1, dense=dense)
     fine.parent = coarse
-    return fine.run(y0, x0, h, w)
+    return fine.run(y0, x0, h, w, dense=dense)
 
 
 class EagerWorld:

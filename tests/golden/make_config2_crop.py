@@ -7,7 +7,7 @@ the decode reads, and in metres (Laplacian decode, Sec. 5.2, App. H).
 
 It calls only the oracle (Eq. 1 brute force on a canvas that holds the whole
 dependency cone of the crop and of the decode's halo: about 18.3k fine and
-17k coarse window evaluations, ~0.65 PFLOP in FP64) and the seeded input
+16.2k coarse window evaluations, ~0.64 PFLOP in FP64) and the seeded input
 generators.  Values are stored as float32 next to the FP64 sigma_out of
 each; the tests compare at 2e-2 sigma_out, far above float32 storage
 rounding.
