@@ -64,7 +64,7 @@ def parse():
                    help="second precision timed on the same workload beside the headline ('' = none)")
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
-    p.add_argument("--pairs", type=int, default=0,
+    p.add_argument("--pairs", type=int, default=1,
                    help="1: tensor-core convolutions on CTA pairs (cta_group::2) where the shape allows")
     p.add_argument("--graphs", type=int, default=1,
                    help="1: the end-to-end leg replays repeated UNet forwards as CUDA graphs")
