@@ -672,23 +672,39 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
     const int q = warp & 3;
     const int row = q * 32 + lane;
     uint32_t acc = 0;
-    // The residual is read one 32-column chunk ahead (the next unit's first
-    // chunk after a unit's last), so its memory latency overlaps the work on
-    // the current chunk.  Each thread still reads every residual element
-    // before it writes the same output element.
+    // Global memory is touched in whole 128-byte pixel chunks: lane l moves
+    // 16-byte piece l % 8 of pixels l / 8, l / 8 + 4, ... of the warp's 32
+    // pixels, and a per-warp shared buffer (32 rows of 36 floats) turns
+    // that into one row per thread (the thread owns its TMEM lane's pixel)
+    // and back.  The residual is read one 32-column chunk ahead (the next
+    // unit's first chunk after a unit's last), so its memory latency
+    // overlaps the work on the current chunk; every residual element is
+    // read before the same output element is written.
+    float* T = reinterpret_cast<float*>(smem + (size_t)STAGES * STAGE_BYTES) + (size_t)q * (32 * 36);
+    const int pc = lane & 7, pr = lane >> 3;  // piece, first pixel of this lane
     float4 nx[8];
-    // element index of pixel m's residual (same grid, or half resolution)
-    auto res_index = [&](int64_t m) -> int64_t {
-      if (!p.res_up) return m;
-      const int64_t w = m / HW, r = m % HW;
-      const int yy = (int)(r / p.W), xx = (int)(r % p.W);
-      return w * (HW / 4) + (int64_t)(yy >> 1) * (p.W >> 1) + (xx >> 1);
-    };
+    // a warp's 32 pixels lie in one window (M tiles are 128-pixel blocks of
+    // windows of 128 k pixels) whose width W is a power of two: their rows
+    // and columns follow from the first pixel's offset with shifts.  The
+    // residual of pixel (y, x) is the same grid's, or (res_up) element
+    // (y / 2, x / 2) of the half-resolution grid.
+    const int wsh = 31 - __clz(p.W);
     auto load_res = [&](int uu, int i, int c) {
-      const int64_t mm = res_index(unit_m0(uu) + i * BM + row);
-      const float4* src = reinterpret_cast<const float4*>(p.res + mm * p.Cout + (uu % p.n_tiles) * BN + c);
+      const int64_t mw = unit_m0(uu) + i * BM + q * 32;  // the warp's first pixel
+      const float* src = p.res + (uu % p.n_tiles) * BN + c + 4 * pc;
+      if (!p.res_up) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) nx[j] = src[j];
+        for (int k = 0; k < 8; ++k) nx[k] = *reinterpret_cast<const float4*>(src + (mw + pr + 4 * k) * p.Cout);
+      } else {
+        const int64_t w0 = mw / HW;
+        const int r0 = (int)(mw - w0 * HW);
+        const int64_t b0 = w0 * (HW / 4);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int rr = r0 + pr + 4 * k, yy = rr >> wsh, xx = rr & (p.W - 1);
+          nx[k] = *reinterpret_cast<const float4*>(src + (b0 + (yy >> 1) * (p.W >> 1) + (xx >> 1)) * p.Cout);
+        }
+      }
     };
     if (p.res && cta0 < n_units) load_res(cta0, 0, 0);
     // PAIR: the accumulator is released on the even CTA's barrier
@@ -701,25 +717,22 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
 #pragma unroll 1
       for (int i = 0; i < MT; ++i) {
         const int64_t m = unit_m0(u) + i * BM + row;
+        const int64_t mw = unit_m0(u) + i * BM + q * 32;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
           float4 rv[8];
           if (p.res) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) rv[j] = nx[j];
+            for (int k = 0; k < 8; ++k) *reinterpret_cast<float4*>(T + (pr + 4 * k) * 36 + 4 * pc) = nx[k];
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) rv[j] = *reinterpret_cast<const float4*>(T + lane * 36 + 4 * j);
             if (c0 + 32 < BN) load_res(u, i, c0 + 32);
             else if (i + 1 < MT) load_res(u, i + 1, 0);
             else if (u + ncta < n_units) load_res(u + ncta, 0, 0);
           }
           uint32_t r[32];
           tmem_ld32(tmem + buf * ACC_COLS + i * BN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-          int64_t mo = m;
-          if (p.out_up) {
-            const int64_t w = m / HW, r = m % HW;
-            const int yy = (int)(r / p.W), xx = (int)(r % p.W);
-            mo = w * (4 * HW) + (int64_t)(2 * yy + p.py) * (2 * p.W) + (2 * xx + p.px);
-          }
-          float* yp = p.y + mo * p.Cout + n0 + c0;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
@@ -727,12 +740,32 @@ __global__ void __launch_bounds__(XF ? 192 + XF_THREADS : 192, 1) conv_tc_kernel
             if (p.res) {
               v.x += rv[j].x; v.y += rv[j].y; v.z += rv[j].z; v.w += rv[j].w;
             }
-            reinterpret_cast<float4*>(yp)[j] = v;
+            *reinterpret_cast<float4*>(T + lane * 36 + 4 * j) = v;
             r[4 * j] = __float_as_uint(v.x);
             r[4 * j + 1] = __float_as_uint(v.y);
             r[4 * j + 2] = __float_as_uint(v.z);
             r[4 * j + 3] = __float_as_uint(v.w);
           }
+          __syncwarp();
+          // the warp's 32 pixels x 32 channels leave in whole 128-byte chunks
+          if (!p.out_up) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              *reinterpret_cast<float4*>(p.y + (mw + pr + 4 * k) * p.Cout + n0 + c0 + 4 * pc) =
+                  *reinterpret_cast<const float4*>(T + (pr + 4 * k) * 36 + 4 * pc);
+          } else {
+            const int64_t w0 = mw / HW;
+            const int r0 = (int)(mw - w0 * HW);
+            const int64_t b0 = w0 * (4 * HW);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int rr = r0 + pr + 4 * k, yy = rr >> wsh, xx = rr & (p.W - 1);
+              const int64_t mo = b0 + (int64_t)(2 * yy + p.py) * (2 * p.W) + (2 * xx + p.px);
+              *reinterpret_cast<float4*>(p.y + mo * p.Cout + n0 + c0 + 4 * pc) =
+                  *reinterpret_cast<const float4*>(T + (pr + 4 * k) * 36 + 4 * pc);
+            }
+          }
+          __syncwarp();  // T is free for the next chunk
           if (p.bstats) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -910,7 +943,8 @@ constexpr int stage_bytes(int BN, bool SPLIT, bool DXR, int MT, bool PAIR = fals
 
 template <int BN, int STAGES, bool SPLIT, bool DXR, bool TF32, int MT, bool XF = false, bool PAIR = false>
 bool launch(const Maps& m, const TcParams& p, cudaStream_t st, std::string* err) {
-  constexpr size_t smem = (size_t)STAGES * stage_bytes(BN, SPLIT, DXR, MT, PAIR) + 1024;
+  // stages, then the epilogue's four 32 x 36-float transpose buffers
+  constexpr size_t smem = (size_t)STAGES * stage_bytes(BN, SPLIT, DXR, MT, PAIR) + 1024 + 4 * 32 * 36 * 4;
   static_assert(smem <= 227 * 1024, "stages exceed the shared memory of a CTA");
   static_assert(2 * MT * BN <= 512, "accumulators exceed tensor memory");
   static bool attr = false;
