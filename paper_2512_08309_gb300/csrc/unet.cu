@@ -1087,6 +1087,68 @@ __global__ void __launch_bounds__(256) conv_out_tile2_kernel(const TA* __restric
 // thread (column, row block) accumulates RPT outputs.  The normalised
 // operand never goes through memory.  Each pass issues all of its global
 // loads before using any of them.
+// The output head: GroupNorm + SiLU + 3x3 convolution of C channels to one,
+// for a tile of HEAD_R output rows of one window.  Pass 1: every pixel of
+// the tile and its one-pixel halo (zero outside the window) is normalised
+// once, and its nine tap contributions z_t = sum_c w[t][c] a[c] are kept in
+// shared memory; pass 2: out(y, x) = sum_t z_t(y + dy_t, x + dx_t).  Each
+// input element is read once (plus the halo rows), so the pass runs at the
+// memory rate.  One thread per pixel in pass 1 (the pixel's C channels as
+// float4 loads).
+constexpr int HEAD_R = 8;
+template <int C>
+__global__ void __launch_bounds__(256) gn_silu_head_kernel(const float* __restrict__ x,
+                                                           const float2* __restrict__ stats,
+                                                           const float* __restrict__ wk,
+                                                           float* __restrict__ y, int H, int W, int G) {
+  extern __shared__ float sm[];
+  const int W2 = W + 2, NP = (HEAD_R + 2) * W2;
+  float* zs = sm;               // [9][NP]
+  float* ws = sm + 9 * NP;      // [9][C]
+  const int r0 = blockIdx.x * HEAD_R;
+  const int64_t b = blockIdx.y;
+  const float* xb = x + b * H * W * C;
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) ws[i] = wk[i];
+  __syncthreads();
+  const int Cg = C / G;
+  for (int pp = threadIdx.x; pp < NP; pp += blockDim.x) {
+    const int ry = pp / W2, rx = pp - ry * W2;
+    const int gy = r0 + ry - 1, gx = rx - 1;
+    float z[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) z[t] = 0.0f;
+    if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+      const float4* src = reinterpret_cast<const float4*>(xb + ((int64_t)gy * W + gx) * C);
+#pragma unroll
+      for (int c4 = 0; c4 < C / 4; ++c4) {
+        const float4 v = src[c4];
+        const float2 ms = stats[b * G + (4 * c4) / Cg];
+        const float a[4] = {silu_fast((v.x - ms.x) * ms.y), silu_fast((v.y - ms.x) * ms.y),
+                            silu_fast((v.z - ms.x) * ms.y), silu_fast((v.w - ms.x) * ms.y)};
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const float4 w4 = *reinterpret_cast<const float4*>(ws + t * C + 4 * c4);
+          z[t] = fmaf(a[0], w4.x, z[t]);
+          z[t] = fmaf(a[1], w4.y, z[t]);
+          z[t] = fmaf(a[2], w4.z, z[t]);
+          z[t] = fmaf(a[3], w4.w, z[t]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) zs[t * NP + pp] = z[t];
+  }
+  __syncthreads();
+  float* yb = y + (b * H + r0) * W;
+  for (int op = threadIdx.x; op < HEAD_R * W; op += blockDim.x) {
+    const int oy = op / W, ox = op - oy * W;
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc += zs[t * NP + (oy + t / 3) * W2 + ox + t % 3];
+    yb[op] = acc;
+  }
+}
+
 template <int RPT>
 __global__ void __launch_bounds__(256) gn_silu_conv_out_kernel(const float* __restrict__ x,
                                                                const float2* __restrict__ stats,
@@ -2344,6 +2406,15 @@ bool out_head(Ctx& c, const float* x, int H, int C, const ConvW& w, float* F, co
   if (c.u->prof) c.u->prof->end(pr, c.st);
   // the fused pass: float32 input read once (with its row halo), F written
   pr = c.u->prof ? c.u->prof->begin(PK_CONV_SIMT, c.st, 2.0 * c.n * HW * 9.0 * C, nb * 4.0 + 4.0 * c.n * HW) : -1;
+  if ((C == 64 || C == 128) && H % HEAD_R == 0) {
+    const size_t hs = ((size_t)9 * (HEAD_R + 2) * (W + 2) + 9 * C) * sizeof(float);
+    auto hk = C == 64 ? gn_silu_head_kernel<64> : gn_silu_head_kernel<128>;
+    cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
+    hk<<<dim3(H / HEAD_R, c.n), 256, hs, c.st>>>(x, c.u->stats, w.w32, F, H, W, G);
+    if (c.u->prof) c.u->prof->end(pr, c.st);
+    c.u->launches++;
+    return true;
+  }
   const size_t smem = ((size_t)8 * (THIN_R + 2) * (W + 2) + 9 * C) * sizeof(float);
   const dim3 grid(H / THIN_R, c.n);
   const int rpt = THIN_R * W / 256;
