@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--impl", default="idf", choices=["idf", "reference"])
     p.add_argument("--query", type=int, default=QUERY)
     p.add_argument("--precision", default="tf32", choices=["bf16", "bf16x3", "tf32", "fp32"])
-    p.add_argument("--also", default="bf16x3", choices=["", "bf16", "bf16x3", "tf32", "fp32"],
+    p.add_argument("--also", default="bf16", choices=["", "bf16", "bf16x3", "tf32", "fp32"],
                    help="second precision timed on the same workload beside the headline ('' = none)")
     p.add_argument("--workspace-gb", type=float, default=0.0, help="UNet workspace (0: library default)")
     p.add_argument("--cache-gb", type=float, default=0.0, help="tile cache (0: library default)")
