@@ -39,7 +39,7 @@ def test_two_level_full_width(case, precision, tol):
 
 
 BF16_MISS = ("plain BF16 does not meet 2e-2 sigma_out on the full-width stack at K = 2 "
-             "(measured max 3.7e-2, rms 8.5e-3 sigma_out): the 2-step result is almost exactly "
+             "(measured max 3.9e-2, rms 8.7e-3 sigma_out): the 2-step result is almost exactly "
              "one network evaluation, so bfloat16 operand rounding (2^-9 through ~25 convolutions) "
              "reaches the output undamped")
 
