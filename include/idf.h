@@ -213,7 +213,11 @@ typedef struct {
  * in_ch != 1, and laplacian = 1 with one level and no fixture) before any
  * device call, IDF_EUNSUPPORTED for IDF_FP8_E4M3 with a level that is not a
  * 16-channel network, IDF_ENOMEM / IDF_ECUDA on
- * device allocation or CUDA failures.  *out is NULL on failure. */
+ * device allocation or CUDA failures.  *out is NULL on failure.  A level
+ * whose in_ch is not 1 (2 under a parent), up to 8, is a side-input network
+ * (a student fed its teacher's noise fields): the world is then
+ * network-only, idf_unet_forward runs its levels and queries return
+ * IDF_EMODEL. */
 idf_status idf_world_create(uint64_t seed, const idf_model_stack* stack,
                             const idf_world_opts* opts, idf_world** out);
 
@@ -419,12 +423,15 @@ void idf_volume_destroy(idf_volume* v);
  * backward kernels (the build's few-step counterpart of the paper's
  * consistency-distilled networks, Sec. 5.4 and App. F "Consistency
  * Distillation").  The network is the UNet of idf_level_desc (same layers and
- * weight order; no attention block; in_ch = out_ch = 1; `window` is the
- * training window size); parameters are float32 master weights.  One
- * training step evaluates D(x; sigma) = c_skip x + c_out S(c_in x) with the
- * EDM coefficients (sigma_data of the descriptor), the loss mean((D - t)^2),
- * and adds d loss / d weights to the student's gradient accumulator.
- * Everything the student holds is owned by the library. */
+ * weight order; no attention block; out_ch = 1, 1 <= in_ch <= 8; `window` is
+ * the training window size); parameters are float32 master weights.  One
+ * training step evaluates D(x; sigma) = c_skip x_0 + c_out S([c_in x_0, x_1,
+ * ..., x_{in_ch - 1}]) with the EDM coefficients (sigma_data of the
+ * descriptor): channel 0 is the noisy state, the others side inputs given
+ * to the network as they are (the teacher's re-noise fields); the loss is
+ * mean((D - t)^2), and d loss / d weights is added to the student's
+ * gradient accumulator.  Everything the student holds is owned by the
+ * library. */
 typedef struct idf_student idf_student;
 
 /* net->weights (n_weights floats, declaration order) are copied as the
@@ -432,7 +439,8 @@ typedef struct idf_student idf_student;
 idf_status idf_student_create(const idf_level_desc* net, int32_t max_batch, int32_t device,
                               idf_student** out);
 
-/* x_dev, target_dev: device float32 (n, window, window); 1 <= n <= max_batch.
+/* x_dev: device float32 (n, in_ch, window, window); target_dev: (n, window,
+ * window); 1 <= n <= max_batch.
  * Writes the batch loss to *loss_out (host) and accumulates its gradient.
  * Ordered after the caller's stream; synchronizes before returning. */
 idf_status idf_student_loss_grad(idf_student* s, const float* x_dev, const float* target_dev,

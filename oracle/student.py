@@ -10,7 +10,9 @@ part is a plain few-step student trained by regression, read as follows:
   parameter order), here written with torch operations in float64 so that
   torch.autograd gives exact gradients;
 * preconditioning as for every denoiser: D(x; sigma) = c_skip x + c_out
-  S(c_in x);
+  S(c_in x); with side inputs (in_ch > 1: x of shape (B, in_ch, H, W))
+  channel 0 is the noisy state and the others are given to S as they are,
+  D = c_skip x_0 + c_out S([c_in x_0, x_1, ...]);
 * loss of a batch at one sigma: mean over pixels of (D(x; sigma) - t)^2,
   where t is the plain sampler's output over the window and x the noisy
   input (pure noise sigma_0 N at sigma = 80, or t + sigma_mid N at
@@ -81,14 +83,24 @@ def forward_torch(lv: dict, p: dict, x: torch.Tensor) -> torch.Tensor:
     return conv(TF.silu(gn(h)), p["out_conv"])
 
 
+def _denoise(lv: dict, p: dict, x: np.ndarray, sigma: float):
+    """D(x; sigma), x (B, H, W) or (B, in_ch, H, W) with side channels."""
+    c_skip, c_out, c_in = S_.edm_coeffs(float(sigma), float(lv["sigma_data"]))
+    xt = torch.as_tensor(np.asarray(x, dtype=np.float64))
+    if xt.dim() == 3:
+        xt = xt[:, None]
+    x0 = xt[:, :1]
+    xin = torch.cat([c_in * x0, xt[:, 1:]], dim=1)
+    return c_skip * x0 + c_out * forward_torch(lv, p, xin)
+
+
 def loss_and_grad(lv: dict, flat: np.ndarray, x: np.ndarray, target: np.ndarray, sigma: float):
     """Loss mean((D(x; sigma) - t)^2) and its gradient w.r.t. the flat weights
-    (declaration order).  x, target: (B, H, W)."""
+    (declaration order).  x: (B, H, W), or (B, in_ch, H, W) with side
+    channels; target: (B, H, W)."""
     p = _params(lv, flat, True)
-    c_skip, c_out, c_in = S_.edm_coeffs(float(sigma), float(lv["sigma_data"]))
-    xt = torch.as_tensor(np.asarray(x, dtype=np.float64))[:, None]
     tt = torch.as_tensor(np.asarray(target, dtype=np.float64))[:, None]
-    D = c_skip * xt + c_out * forward_torch(lv, p, c_in * xt)
+    D = _denoise(lv, p, x, sigma)
     loss = ((D - tt) ** 2).mean()
     loss.backward()
     g = torch.cat([p[n].grad.reshape(-1) for n, _ in U_.param_shapes(lv)])
@@ -98,10 +110,8 @@ def loss_and_grad(lv: dict, flat: np.ndarray, x: np.ndarray, target: np.ndarray,
 def loss_only(lv: dict, flat: np.ndarray, x: np.ndarray, target: np.ndarray, sigma: float) -> float:
     with torch.no_grad():
         p = _params(lv, flat, False)
-        c_skip, c_out, c_in = S_.edm_coeffs(float(sigma), float(lv["sigma_data"]))
-        xt = torch.as_tensor(np.asarray(x, dtype=np.float64))[:, None]
         tt = torch.as_tensor(np.asarray(target, dtype=np.float64))[:, None]
-        D = c_skip * xt + c_out * forward_torch(lv, p, c_in * xt)
+        D = _denoise(lv, p, x, sigma)
         return float(((D - tt) ** 2).mean())
 
 

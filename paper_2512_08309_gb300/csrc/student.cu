@@ -5,7 +5,9 @@
 // The network is the ResBlock UNet of unet.cu (same layer reading and weight
 // order, no attention block).  A training step evaluates
 //   D(x; sigma) = c_skip x + c_out S(c_in x),  loss = mean((D - t)^2)
-// and accumulates dloss/dw; AdamW applies the accumulated gradient.
+// and accumulates dloss/dw; AdamW applies the accumulated gradient.  With
+// in_ch > 1 the input x (NCHW) carries the noisy state in channel 0 and side
+// inputs in the others: D = c_skip x_0 + c_out S([c_in x_0, x_1, ...]).
 //
 // Engine: the forward runs as a tape of ops (conv, GroupNorm+SiLU, pool,
 // upsample-concat) that keeps every activation; the backward walks the tape in
@@ -262,21 +264,29 @@ __global__ void add_kernel(const float* __restrict__ a, int64_t n_el, float* __r
     y[i] += a[i];
 }
 
-__global__ void scale_kernel(const float* __restrict__ a, float s, int64_t n_el, float* __restrict__ y) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_el; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = s * a[i];
+// NCHW x -> NHWC network input: channel 0 scaled by c_in, side channels as they are
+__global__ void precond_in_kernel(const float* __restrict__ x, float c_in, int64_t npx, int HW, int C,
+                                  float* __restrict__ y) {
+  const int64_t n_el = npx * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_el; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t m = i / C, b = m / HW, px = m % HW;
+    const float v = x[(b * C + c) * HW + px];
+    y[i] = c == 0 ? c_in * v : v;
+  }
 }
 
 // D = c_skip x + c_out F; per-block sums of (D - t)^2 in double; gF = 2 c_out (D - t) / N
+// (x: channel 0 of the NCHW input, C channels of HW pixels per window)
 __global__ void __launch_bounds__(256) mse_kernel(const float* __restrict__ x, const float* __restrict__ F,
                                                   const float* __restrict__ t, int64_t N, float c_skip,
                                                   float c_out, float* __restrict__ gF,
-                                                  double* __restrict__ block_sums) {
+                                                  double* __restrict__ block_sums, int HW, int C) {
   __shared__ double red[256];
   double s = 0.0;
   const float k = 2.0f * c_out / (float)N;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = c_skip * x[i] + c_out * F[i] - t[i];
+    const float d = c_skip * x[(i / HW) * C * HW + i % HW] + c_out * F[i] - t[i];
     s += (double)d * d;
     gF[i] = k * d;
   }
@@ -479,7 +489,7 @@ idf_status idf_student_create(const idf_level_desc* net, int32_t max_batch, int3
   if (!out) return IDF_EINVAL;
   *out = nullptr;
   if (!net || max_batch < 1 || net->levels < 1 || net->levels > 6 || !net->channels || net->attn_at_bottom ||
-      net->in_ch != 1 || net->out_ch != 1 || net->gn_groups < 1 || net->window < 2 ||
+      net->in_ch < 1 || net->in_ch > 8 || net->out_ch != 1 || net->gn_groups < 1 || net->window < 2 ||
       net->window % (1 << (net->levels - 1)) || !(net->sigma_data > 0))
     return IDF_EINVAL;
   for (int l = 0; l < net->levels; ++l)
@@ -495,7 +505,7 @@ idf_status idf_student_create(const idf_level_desc* net, int32_t max_batch, int3
   idf_student* s = new idf_student();
   s->d.levels = net->levels;
   s->d.ch.assign(net->channels, net->channels + net->levels);
-  s->d.in_ch = 1;
+  s->d.in_ch = net->in_ch;
   s->d.out_ch = 1;
   s->d.groups = net->gn_groups;
   s->d.attn = 0;
@@ -561,7 +571,8 @@ idf_status idf_student_loss_grad(idf_student* s, const float* x_dev, const float
   const int H = s->d.window;
   const int64_t npx = (int64_t)n * H * H;
   // ---- forward
-  scale_kernel<<<grid_n(npx, 256), 256, 0, st>>>(x_dev, c_in, npx, A(s, s->buf_x));
+  precond_in_kernel<<<grid_n(npx * s->d.in_ch, 256), 256, 0, st>>>(x_dev, c_in, npx, H * H, s->d.in_ch,
+                                                                   A(s, s->buf_x));
   for (const SOp& op : s->ops) {
     const SBuf& bi = s->bufs[op.in];
     switch (op.kind) {
@@ -588,7 +599,8 @@ idf_status idf_student_loss_grad(idf_student* s, const float* x_dev, const float
   // ---- loss and dF
   if (!ck(s, cudaMemsetAsync(s->grad, 0, s->per_window * s->max_batch * 4, st), "memset grad")) return IDF_ECUDA;
   const int nb = std::min<int64_t>(1024, (npx + 255) / 256);
-  mse_kernel<<<nb, 256, 0, st>>>(x_dev, A(s, s->buf_F), t_dev, npx, c_skip, c_out, Gd(s, s->buf_F), s->loss_parts);
+  mse_kernel<<<nb, 256, 0, st>>>(x_dev, A(s, s->buf_F), t_dev, npx, c_skip, c_out, Gd(s, s->buf_F), s->loss_parts,
+                                 H * H, s->d.in_ch);
   // ---- backward
   for (int oi = (int)s->ops.size() - 1; oi >= 0; --oi) {
     const SOp& op = s->ops[oi];

@@ -248,7 +248,10 @@ std::string check_level(const idf_level_desc& d, int index) {
   if (d.steps < 1 || d.steps > 64) return bad("steps must be in [1, 64]");
   if (!(d.sigma_max > 0) || !(d.sigma_min > 0) || !(d.sigma_data > 0) || !(d.rho > 0)) return bad("sigmas must be positive");
   if (d.out_ch != 1) return bad("out_ch must be 1");
-  if (d.in_ch != (d.scale_to_parent > 0 ? 2 : 1)) return bad("in_ch must be 1, or 2 for a conditioned level");
+  // in_ch 1 (2 with a parent) for a level the sampler runs; other widths
+  // (side-input networks, e.g. a student fed the teacher's noise fields)
+  // make a network-only world: idf_unet_forward runs, queries do not
+  if (d.in_ch < 1 || d.in_ch > 8) return bad("in_ch must be in [1, 8]");
   if (d.scale_to_parent > 0 && index == 0) return bad("the first level has no parent");
   if (d.test_denoiser < 0 || d.test_denoiser > 3) return bad("test_denoiser must be 0..3");
   if (d.n_rounds < 0 || (d.n_rounds > 0 && !d.round_steps)) return bad("round_steps missing");
@@ -969,6 +972,9 @@ struct Req {
 // Serve requests (all of one output kind) on the world's stream.
 idf_status serve(idf_world* W, const std::vector<Req>& reqs, idf_output_kind kind) {
   if (W->poisoned) return fail(W, IDF_EINTERNAL, "world unusable after an earlier CUDA failure: " + W->last_error);
+  for (const Level& L : W->lv)
+    if (L.d.in_ch != (L.d.scale_to_parent > 0 ? 2 : 1))
+      return fail(W, IDF_EMODEL, "a level with side-input channels runs only through idf_unet_forward");
   const int nl = (int)W->lv.size();
   if (kind == IDF_OUT_METRES && !W->stack.laplacian)
     return fail(W, IDF_EINVAL, "IDF_OUT_METRES needs a stack with laplacian = 1");

@@ -49,6 +49,24 @@ def test_loss_and_gradient_match_oracle(idf, lv, n, sigma):
     assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g))
 
 
+def test_side_channel_loss_and_gradient_match_oracle(idf):
+    # in_ch = 4: the noisy state in channel 0, three side fields unscaled
+    lv = synth.level(levels=2, channels=(8, 16), in_ch=4, out_ch=1, window=16, gn_groups=4)
+    w = _w(lv, 5)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((3, 4, 16, 16)).astype(np.float32)
+    x[:, 0] *= 80.0
+    t = (rng.standard_normal((3, 16, 16)) * 0.3).astype(np.float32)
+    S = idf.Student(lv, w, max_batch=4)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss = S.loss_grad(xd.data_ptr(), td.data_ptr(), 3, 80.0)
+    g = S.grads().astype(np.float64)
+    S.close()
+    ref_loss, ref_g = OST.loss_and_grad(lv, w.astype(np.float64), x, t, 80.0)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g))
+
+
 def test_student_width_gradient_matches_oracle(idf):
     # the student of the distillation (32/64/128/128 channels, 128x128 windows)
     lv = synth.student_level()
