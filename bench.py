@@ -74,6 +74,8 @@ def parse():
                    help="distillation mode: train the student on N pairs from the plain sampler, judge it")
     p.add_argument("--epochs", type=int, default=4)
     p.add_argument("--student-query", type=int, default=2048)
+    p.add_argument("--student-window", type=int, default=128,
+                   help="student window side (128: the 128/64 student; 32: one teacher tile per window)")
     p.add_argument("--serve", type=int, default=0,
                    help="serving mode: N random-access queries on the plain 16-channel stack, batched vs one by one")
     p.add_argument("--in-flight", type=int, default=64)
@@ -722,7 +724,7 @@ def run_student(args):
     import paper_2512_08309_gb300 as idf
     import synth
     dev = torch.device("cuda", 0)
-    n_pairs, H = args.student, 128
+    n_pairs, H = args.student, args.student_window
     c1 = synth.config1_stack()
     tlv = dict(c1["level"][0], stride=int(c1["level"][0]["window"]))
     tst = synth.stack([tlv])
@@ -752,7 +754,7 @@ def run_student(args):
     n_hold = max(64, n_pairs // 16)
     n_train = n_pairs - n_hold
     sig_out = float(T[n_train:].std())
-    lv = dict(synth.student_level(), in_ch=4)
+    lv = dict(synth.student_level(window=H, stride=H // 2), in_ch=4)
     w0 = synth.weights(idf.param_shapes(lv), 0, 0)
     bs = 64
     S = idf.Student(lv, w0, max_batch=bs)
