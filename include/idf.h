@@ -47,7 +47,7 @@ typedef enum {
   IDF_EMODEL = 5,        /* weights do not match the described network */
   IDF_EDEVICE_CHECK = 6, /* a device-side bounds check fired */
   IDF_EINTERNAL = 7,     /* world poisoned by an earlier failure, or a bug */
-  IDF_EUNSUPPORTED = 8   /* valid request that this build does not implement */
+  IDF_EUNSUPPORTED = 8   /* valid request that this library does not implement */
 } idf_status;
 
 /* Arithmetic of the UNet convolutions.  IDF_FP32: float32 SIMT (the plain
@@ -420,7 +420,7 @@ void idf_volume_destroy(idf_volume* v);
 /* ------------------------------------------------------ learned student */
 
 /* A student denoiser trained on the GPU by this library's own forward and
- * backward kernels (the build's few-step counterpart of the paper's
+ * backward kernels (the library's few-step counterpart of the paper's
  * consistency-distilled networks, Sec. 5.4 and App. F "Consistency
  * Distillation").  The network is the UNet of idf_level_desc (same layers and
  * weight order; no attention block; out_ch = 1, 1 <= in_ch <= 8; `window` is

@@ -3,7 +3,7 @@
 Test infrastructure (see the package header).
 
 The paper distils its networks into few-step continuous-time consistency
-models (Sec. 5.4, App. F "Consistency Distillation"); the build's learned
+models (Sec. 5.4, App. F "Consistency Distillation"); the learned
 part is a plain few-step student trained by regression, read as follows:
 
 * network S: the same ResBlock UNet as ``oracle.unet`` (its layer reading and

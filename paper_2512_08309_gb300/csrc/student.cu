@@ -1,5 +1,5 @@
 // Learned student denoiser: training on the GPU with the library's own
-// forward and backward kernels (the build's counterpart of the paper's few-step
+// forward and backward kernels (the library's counterpart of the paper's few-step
 // distilled models, Sec. 5.4 / App. F "Consistency Distillation").
 //
 // The network is the ResBlock UNet of unet.cu (same layer reading and weight
