@@ -13,6 +13,7 @@ each; the tests compare at 2e-2 sigma_out, far above float32 storage
 rounding.
 
     python tests/golden/make_config2_crop.py [processes]
+    python tests/golden/make_config2_crop.py 7 -128 -128 256 256 config2_crop_k20_origin.npz
 """
 import os
 import sys
@@ -62,4 +63,10 @@ def main(processes: int, steps: int = STEPS, crop=CROP, out_name="config2_crop_k
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else os.cpu_count())
+    # make_config2_crop.py [processes] [x0 y0 w h out_name]
+    a = sys.argv[1:]
+    procs = int(a[0]) if a else os.cpu_count()
+    if len(a) >= 6:
+        main(procs, crop=(int(a[1]), int(a[2]), int(a[3]), int(a[4])), out_name=a[5])
+    else:
+        main(procs)
