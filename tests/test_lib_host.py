@@ -100,3 +100,24 @@ def test_world_create_accepts_a_single_level_low_band_setup():
         idf.World(0, st, [None]).close()
     except idf.IdfError as e:
         assert e.status == idf.IDF_ECUDA
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # with libidf absent the binding raises on its first call: there is no
+    # other implementation behind it (a subprocess, so that the library this
+    # process has loaded stays untouched)
+    import subprocess
+    import sys
+    code = ("import paper_2512_08309_gb300 as idf, synth\n"
+            f"idf.LIB_PATH = {str(tmp_path / 'absent' / 'libidf.so')!r}\n"
+            "for call in (lambda: idf.lib(), lambda: idf.World(0, synth.config2_stack(), [None, None])):\n"
+            "    try:\n"
+            "        call()\n"
+            "    except RuntimeError as e:\n"
+            "        assert 'not built' in str(e), e\n"
+            "    else:\n"
+            "        raise SystemExit('no error without the library')\n")
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
