@@ -37,6 +37,7 @@ _conv, _gn, _silu, _pool, _up2, _attn, _cbias = (U.conv, U.group_norm, U.silu, U
 _taps, _down = L.blur_taps, L.down_mean
 _lossg = OST.loss_and_grad
 _kappa3, _conv3 = V.kappa3, V.conv3
+_net, _init = S._LevelCommon.net, S._LevelCommon.__init__
 
 
 def _shim(module, **over):
@@ -83,6 +84,36 @@ def _denoise_side_scaled(lv, p, x, sigma):
     if xt.dim() == 3:
         xt = xt[:, None]
     return c_skip * xt[:, :1] + c_out * OST.forward_torch(lv, p, c_in * xt)
+
+
+def _cond_rounded(self, y0, x0, h, w):
+    # the parent pixel of a fine pixel taken by rounding instead of flooring
+    f = self.scale
+    ys, xs = (np.arange(y0, y0 + h) + f // 2) // f, (np.arange(x0, x0 + w) + f // 2) // f
+    P = self.parent.final(ys[0], xs[0], ys[-1] - ys[0] + 1, xs[-1] - xs[0] + 1)
+    return P[np.ix_(ys - ys[0], xs - xs[0])]
+
+
+def _net_roles_swapped(self, xin, ys):
+    # AutoGuidance with the main and guide networks in each other's place
+    if self.guide is None:
+        return _net(self, xin, ys)
+    self.params, self.guide = self.guide, self.params
+    try:
+        return _net(self, xin, ys)
+    finally:
+        self.params, self.guide = self.guide, self.params
+
+
+def _init_blend_every_step(self, *a, **k):
+    # the round grouping ignored: Eq. 2 after every sampler step
+    _init(self, *a, **k)
+    self.round_steps, self.R, self.round_start = [1] * self.K, self.K, list(range(self.K))
+
+
+def _rounds_pin():
+    with pytest.MonkeyPatch.context() as mp:
+        TS.test_rounds_nonlinear_local_denoiser_closed_form(mp, (2, 2))
 
 
 ATTN_LV = synth.level(levels=3, channels=(8, 16, 16), in_ch=2, attn_at_bottom=1, attn_heads=2, window=16)
@@ -135,6 +166,12 @@ CASES = [
     ("flat_blend_window",
      lambda mp: mp.setattr(S, "S_", _shim(Sc, weight_2d=lambda size, eps: np.ones((size, size)))),
      [TS.test_local_coordinate_denoiser_closed_form]),
+    ("conditioning_parent_pixel_rounded", _set(S._LevelCommon, "cond", _cond_rounded),
+     [TS.test_conditioning_closed_form_two_level]),
+    ("guidance_roles_swapped", _set(S._LevelCommon, "net", _net_roles_swapped),
+     [TS.test_guidance_is_affine_in_the_scale_for_one_step]),
+    ("rounds_ignored", _set(S._LevelCommon, "__init__", _init_blend_every_step),
+     [_rounds_pin]),
     # the window denoiser (UNet)
     ("conv_kernel_flipped", _set(U, "conv", lambda x, w: _conv(x, w[:, :, ::-1, ::-1])),
      [TU.test_conv_is_cross_correlation]),

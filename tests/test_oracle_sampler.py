@@ -288,6 +288,66 @@ def test_rounds_local_coordinate_closed_form(rounds):
     assert np.max(np.abs(got - J)) < 1e-12 * np.max(np.abs(J))
 
 
+def _rounds_by_pixel(lv, rounds, seed, rect, F):
+    """Blending only at round ends, written out per pixel and per covering
+    window: each of the 2 x 2 windows over a pixel runs its own trajectory
+    x <- c_skip x + c_out F(c_in x, g) + sigma_{j+1} N through the round, g
+    the window-local coordinate term u/H - 2 v/H."""
+    H, s, K_ = lv["window"], lv["stride"], lv["steps"]
+    y0, x0, h, w = rect
+    sig = Sc.sigmas(K_, lv["sigma_max"], lv["sigma_min"], lv["rho"])
+    w1 = Sc.weight_1d(H, 1e-3)
+    Y = np.arange(y0, y0 + h)[:, None] + np.zeros((1, w), dtype=np.int64)
+    X = np.arange(x0, x0 + w)[None, :] + np.zeros((h, 1), dtype=np.int64)
+    noise = [N.normal_region(seed, 0, j, x0, y0, w, h).astype(np.float64) for j in range(K_)]
+    J = sig[0] * noise[0]
+    j0 = 0
+    for m in rounds:
+        num = np.zeros((h, w))
+        den = np.zeros((h, w))
+        for di in (0, 1):
+            for dj in (0, 1):
+                u = Y - (Y // s - di) * s
+                v = X - (X // s - dj) * s
+                ww = w1[u] * w1[v]
+                g = u / H - 2.0 * v / H
+                x = J.copy()
+                for j in range(j0, j0 + m):
+                    cs, co, ci = Sc.edm_coeffs(sig[j], lv["sigma_data"])
+                    x = cs * x + co * F(ci * x, g)
+                    if j + 1 < K_:
+                        x = x + sig[j + 1] * noise[j + 1]
+                num += ww * x
+                den += ww
+        J = num / den
+        j0 += m
+    return J
+
+
+@pytest.mark.parametrize("rounds", [(2, 2), (3, 1)])
+def test_rounds_nonlinear_local_denoiser_closed_form(monkeypatch, rounds):
+    # With a denoiser affine in x (the test denoisers), blending after every
+    # step and blending at round ends agree: the blend is a normalised linear
+    # combination, and it commutes with affine maps whose coefficients all
+    # windows share.  A denoiser nonlinear in x and dependent on the window,
+    # F = tanh(c_in x) + u/H - 2 v/H, tells the two apart.
+    def nonlinear_local(kind, x):
+        B, C, H, W = x.shape
+        u = np.arange(H, dtype=np.float64)[:, None] / H
+        v = np.arange(W, dtype=np.float64)[None, :] / W
+        return np.tanh(x.sum(axis=1, keepdims=True)) + (u - 2.0 * v)[None, None]
+    monkeypatch.setattr(U, "test_denoiser", nonlinear_local)
+    st = _rounds(synth.config1_stack(test_denoiser=3), rounds)
+    lv = st["level"][0]
+    rect = (-23, 40, 19, 21)
+    got = S.World(5, st, None).model(rect[0], rect[1], rect[2], rect[3])
+    F = lambda xin, g: np.tanh(xin) + g   # noqa: E731
+    ref = _rounds_by_pixel(lv, rounds, 5, rect, F)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    every = _rounds_by_pixel(lv, (1,) * lv["steps"], 5, rect, F)
+    assert np.max(np.abs(every - ref)) > 1e-4 * np.max(np.abs(ref))
+
+
 def test_rounds_lazy_equals_eager_and_cone_counts():
     st = _rounds(synth.config1_stack(), (2, 2))
     wts = _weights(st)
