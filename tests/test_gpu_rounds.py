@@ -2,9 +2,14 @@
 sampler steps grouped into rounds, each window running a round's steps on
 its own and Eq. 2 blending the windows at the round's end.  Checked against
 the FP64 oracle's literal per-window rounds: the 16-channel UNet (FP32 and
-the fused BF16 kernel), the local-coordinate test denoiser (whose per-window
-trajectories differ, so a wrong round grouping shows), a two-level stack,
-and the windows evaluated per round (the cone advances by rounds)."""
+the fused BF16 kernel; the network is nonlinear, so a wrong round grouping
+shows: in the oracle, (2, 2), (4,) and (1, 3) differ from blending after
+every step by 1.6e-2, 4.8e-2 and 4.9e-2 sigma_out on the FP32 case's
+region, against its 1e-4 bound), the local-coordinate test denoiser (per-window trajectories that
+differ by window; being affine in x it gives the same result for any
+grouping, so it checks the window-local steps, not the grouping), a
+two-level stack, and the windows evaluated per round (the cone advances by
+rounds)."""
 import numpy as np
 import pytest
 
