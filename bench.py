@@ -91,6 +91,8 @@ def parse():
                         "(--small-precision)")
     p.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                    help="where the nvidia-smi clock samples of the timed region are written")
+    p.add_argument("--ref-seconds", type=float, default=10.0,
+                   help="reference arm: seconds of oracle window evaluations sampled per step")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--fp32-steps", type=int, default=1,
@@ -281,10 +283,10 @@ def run_reference(args, rank, world):
     vals = []
     desc = None
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state
+        oracle_sample(seconds=min(2.0, args.ref_seconds))   # untimed: pages in the oracle and BLAS
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        px, desc, threads, _ = oracle_sample(seconds=10.0)
+        px, desc, threads, _ = oracle_sample(seconds=args.ref_seconds)
         vals.append(px)
     elapsed = time.perf_counter() - t_all
     v = statistics.median(vals)
