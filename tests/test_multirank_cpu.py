@@ -1,6 +1,7 @@
 """The multi-GPU path of bench.py on CPU: world_size 2 with gloo.  Every rank
 serves its own regions (weak scaling, no collective on the data path); the
-ranks meet only in the barrier and the max-over-ranks of the timed interval."""
+ranks meet only in the barrier and the max-over-ranks of the timed interval.
+The reference arm launched the same way prints its line from rank 0 only."""
 import os
 import socket
 
@@ -53,3 +54,22 @@ def test_two_ranks_gloo():
         for j in range(i + 1, len(boxes)):
             (x1, y1), (x2, y2) = boxes[i], boxes[j]
             assert abs(x1 - x2) >= span or abs(y1 - y2) >= span
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    # launched as the multi-GPU run is (torchrun, two ranks, gloo here): rank
+    # 0 alone times the oracle and prints the line, the other rank exits 0
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "1", "--ref-seconds", "0.2"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, OMP_NUM_THREADS="2"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
