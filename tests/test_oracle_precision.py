@@ -1,0 +1,66 @@
+"""Operand precision against the 2e-2 sigma_out bound, on the CPU.
+
+The FP64 oracle network with the operands of its 64-256-channel
+convolutions rounded to a narrower significand (round to nearest even; the
+in-conv and the output head stay unrounded, as the tensor-core path runs
+them in float32 SIMT) shows what operand rounding alone costs one window
+of the two-level stack's networks, before any kernel is involved:
+bfloat16 operands (8 significant bits) put the output about 0.6-0.85% rms
+and 3.4-4.3% max of sigma_out away from the FP64 network, above the bound;
+tf32 operands (11 significant bits) stay near 0.1% rms and 0.5% max.  A
+bfloat16 kernel cannot meet the bound on these networks, a tf32 one can."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import unet as U
+
+torch = pytest.importorskip("torch")
+
+
+def round_significand(a, bits):
+    """a rounded to float32, then to `bits` explicit significand bits (round
+    to nearest, ties to even)."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    drop = 23 - bits
+    r = (b + ((1 << (drop - 1)) - 1) + ((b >> drop) & 1)) & ~np.uint64((1 << drop) - 1)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_rounding_equals_torch_bfloat16_conversion():
+    # 7 explicit bits is bfloat16: the same values as the library's
+    # round-to-nearest-even float32 -> bfloat16 conversion
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(100000) * 10.0 ** rng.integers(-20, 20, 100000),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.01171875, -3.0e38])]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(round_significand(x, 7), ref)
+
+
+def _emulated(lv, p, x, bits, monkeypatch):
+    conv = U.conv
+
+    def rounded_conv(a, w):
+        if a.shape[1] == lv["in_ch"] or w.shape[0] == lv["out_ch"]:
+            return conv(a, w)
+        return conv(round_significand(a, bits), round_significand(w, bits))
+    with monkeypatch.context() as m:
+        m.setattr(U, "conv", rounded_conv)
+        return U.forward(lv, p, x)
+
+
+@pytest.mark.parametrize("li", [0, 1])
+def test_bfloat16_operands_miss_and_tf32_operands_meet_the_bound(monkeypatch, li):
+    st = synth.config2_stack()
+    lv = st["level"][li]
+    p = U.unpack(lv, synth.weights([s for _, s in U.param_shapes(lv)], 0, li))
+    x = synth.window_batch(2, lv["in_ch"], lv["window"], seed=li)
+    ref = U.forward(lv, p, x)
+    err = {}
+    for name, bits in (("bf16", 7), ("tf32", 10)):
+        d = _emulated(lv, p, x, bits, monkeypatch) - ref
+        err[name] = (float(np.sqrt(np.mean(d * d)) / ref.std()), float(np.max(np.abs(d)) / ref.std()))
+        print(f"level {li} {name} operands: rms {err[name][0]:.2e}, max {err[name][1]:.2e} sigma_out")
+    assert err["bf16"][1] > 2e-2 and err["bf16"][0] > 4e-3
+    assert err["tf32"][1] < 1e-2 and err["tf32"][0] < 2e-3
