@@ -1,5 +1,7 @@
 """The full 20-step configuration of the 2-level stack against the FP64
-oracle, element by element, on the 256 x 256 crop at (1920, 1920).
+oracle, element by element, on 256 x 256 crops: at (1920, 1920), and at
+(-128, -128) across the origin (negative tile indices and their floor
+division at the full width and step count).
 
 The expected values were written once by tests/golden/make_config2_crop.py,
 which calls only the oracle (Eq. 1 brute force over the crop's whole
@@ -21,18 +23,20 @@ from oracle import unet as OU
 
 pytestmark = pytest.mark.gpu
 
-FIX = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config2_crop_k20.npz")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+FIXTURES = ["config2_crop_k20.npz", "config2_crop_k20_origin.npz"]
 
-BF16_MISS = ("plain BF16 misses 2e-2 sigma_out at the full 20 steps: measured 7.8e-2 sigma_out (fine), "
-             "2.4e-2 (coarse), 2.2 m in metres; bfloat16 operand rounding through ~25 convolutions per "
+BF16_MISS = ("plain BF16 misses 2e-2 sigma_out at the full 20 steps: measured at (1920, 1920) 7.8e-2 "
+             "sigma_out (fine), 2.4e-2 (coarse), 2.2 m in metres; bfloat16 operand rounding through ~25 convolutions per "
              "network evaluation, compounded over the 20 evaluations of the chain (1.9e-2 at 4 steps)")
 
 
-@pytest.fixture(scope="module")
-def fix():
-    if not os.path.exists(FIX):
-        pytest.skip("the oracle fixture has not been written (tests/golden/make_config2_crop.py)")
-    d = np.load(FIX)
+@pytest.fixture(scope="module", params=FIXTURES)
+def fix(request):
+    path = os.path.join(GOLDEN, request.param)
+    if not os.path.exists(path):
+        pytest.skip(f"the oracle fixture {request.param} has not been written (tests/golden/make_config2_crop.py)")
+    d = np.load(path)
     st = synth.config2_stack(steps=int(d["steps"]))
     wts = [synth.weights([s for _, s in OU.param_shapes(lv)], 0, i) for i, lv in enumerate(st["level"])]
     import paper_2512_08309_gb300 as idf
