@@ -27,7 +27,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 FIXTURES = ["config2_crop_k20.npz", "config2_crop_k20_origin.npz"]
 
 BF16_MISS = ("plain BF16 misses 2e-2 sigma_out at the full 20 steps: measured at (1920, 1920) 7.8e-2 "
-             "sigma_out (fine), 2.4e-2 (coarse), 2.2 m in metres; bfloat16 operand rounding through ~25 convolutions per "
+             "sigma_out (fine), 2.4e-2 (coarse), 2.2 m in metres, and at (-128, -128) 5.3e-2 (fine), 1.2e-2 "
+             "(coarse), 0.54 m; bfloat16 operand rounding through ~25 convolutions per "
              "network evaluation, compounded over the 20 evaluations of the chain (1.9e-2 at 4 steps)")
 
 
